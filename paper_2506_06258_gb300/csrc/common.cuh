@@ -1,0 +1,257 @@
+// Internal declarations shared by the libpdhcg translation units.
+//
+// Data layout in HBM (one market, n buyers, m goods, nnz utilities):
+//   rp[n+1]  int64   row pointers (copy of the caller's)
+//   cj[nnz]  int32   good id of each entry, RELABELLED by decreasing column
+//                    degree (rank 0 = most popular good) so that the hot goods
+//                    are ids [0, H) and their column sums live in shared memory
+//   uv[nnz]  V       row-scaled utilities u_ij / max_j u_ij (Section 5)
+//   X0,X1    V       x^k and x^{k+1} (ping-pong, roles in Ctl::cur)
+//   Xb       V       running average x-bar (Alg. 2)
+//   Xr       V       x at the last restart (primal-weight update)
+// with V = float (MIXED) or double (FP64).  Per-good vectors are double and sit
+// in L2 (m * 8 B each).  Column sums are accumulated exactly as 64-bit fixed
+// point (MIXED) or as FP64 atomics (FP64).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include "../../include/pdhcg.h"
+
+namespace pdhcg {
+
+// ---------------------------------------------------------------------------
+// constants
+// ---------------------------------------------------------------------------
+constexpr double kFixScale = 1099511627776.0;          // 2^40
+constexpr double kFixInv = 1.0 / 1099511627776.0;
+constexpr float kFixScaleF = 1099511627776.0f;
+constexpr int kWarps = 8;                               // warps per block of the row kernels
+constexpr int kThreads = kWarps * 32;
+constexpr int kMaxBuckets = 8;
+constexpr int kSlots = 4;                               // entries per lane held in registers
+
+// ---------------------------------------------------------------------------
+// iteration control block (device resident; one per solve)
+// ---------------------------------------------------------------------------
+struct Ctl {
+    // step control (Section 5: tau = eta/omega, sigma = eta*omega)
+    double eta, omega, eta0, eta_min, eta_max_abs;
+    double tau, sigma;
+    double sum_eta;        // sum of step sizes since the last restart (average weights)
+    double fold_wgt;       // weight with which x^k is folded into the average
+    double eta_used;       // step size of the last accepted pass
+    int fold_pending;      // the last pass was accepted: fold x^k, commit p
+    int accepted;          // last pass accepted
+    int cur;               // X buffer holding x^k
+    int ck, ckm1, cnew;    // roles of the three column-sum buffers
+    int active;            // 0: kernels return immediately (quota reached / stopped)
+    int nan_flag;
+    long long iters;       // accepted iterations in total
+    long long passes;      // row passes in total
+    long long chunk_acc;   // accepted iterations in the current chunk
+    long long chunk_quota; // accepted iterations wanted per chunk
+    long long capped;      // rows whose solve hit the round cap
+    unsigned int ticket;   // last-block-done counter of the dual kernel
+    unsigned int ticket2;  // last-block-done counter of the KKT goods kernel
+    int row_cap;           // active-set rounds per row solve
+    int pad;
+};
+
+// Results of one KKT evaluation (written by the KKT goods kernel's last block).
+struct KktOut {
+    double r_primal, r_dual, r_gap, kkt;
+};
+
+// Per-block partial maxima / sums of the KKT row kernel.
+struct KktPart {
+    double max_x, max_g, max_xg, max_y;
+};
+
+struct Bucket {
+    int g;          // lanes per row (4, 8, 16, 32)
+    int chunks;     // 0 = row fits in registers (g * kSlots), else multi-chunk
+    long long first, count;   // range in row_order
+};
+
+// ---------------------------------------------------------------------------
+// float-float ("double-single") arithmetic: an unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2, giving about 48 significant bits.  Built from
+// the error-free transformations TwoSum (Knuth) and TwoProduct via FMA
+// (Dekker's product, exact with a fused multiply-add).
+// ---------------------------------------------------------------------------
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_make(float h, float l) { ff r; r.hi = h; r.lo = l; return r; }
+__device__ __forceinline__ ff ff_from_double(double d) {
+    float h = (float)d;
+    return ff_make(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// s + e = a + b exactly
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff_make(s, e);
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return ff_make(s, e);
+}
+// p + e = a * b exactly
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return ff_make(p, e);
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff_make(-a.hi, -a.lo); }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    ff s = two_sum(a.hi, b);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    ff p = two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, p.lo);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p.hi, e);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    ff p = two_prod(a.hi, b);
+    float e = __fmaf_rn(a.lo, b, p.lo);
+    return quick_two_sum(p.hi, e);
+}
+// a / b with one correction step
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    ff r = ff_sub(a, ff_mul_f(b, q1));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return quick_two_sum(q1, q2);
+}
+// sqrt with one Newton correction: y + (a - y^2) / (2y)
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+    if (!(a.hi > 0.0f)) return ff_make(0.0f, 0.0f);
+    float y = __fsqrt_rn(a.hi);
+    ff e = ff_sub(a, two_prod(y, y));
+    return quick_two_sum(y, __fdiv_rn(e.hi, __fmul_rn(2.0f, y)));
+}
+__device__ __forceinline__ bool ff_pos(ff a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
+
+// ---------------------------------------------------------------------------
+// misc device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long dbits(double d) { return (unsigned long long)__double_as_longlong(d); }
+
+// max of non-negative doubles through their bit patterns
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
+    if (v > 0.0) atomicMax(a, dbits(v));
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ ff group_sum(ff v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        ff w = ff_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+        v = ff_add(v, w);
+    }
+    return v;
+}
+template <int G>
+__device__ __forceinline__ bool group_any(bool b) {
+    unsigned bal = __ballot_sync(0xffffffffu, b);
+    int lane = threadIdx.x & 31;
+    unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    return (bal & gm) != 0u;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in prox.cu, kkt.cu, prep.cu)
+// ---------------------------------------------------------------------------
+struct DevMarket {
+    int n, m;
+    long long nnz;
+    const long long* rp;
+    const int* cj;
+    const void* uv;        // float or double
+    const double* w;
+    const int* row_order;  // rows grouped by degree bucket
+    Bucket buckets[kMaxBuckets];
+    int nb;
+    int hot;               // goods [0, hot) accumulate in shared memory
+    int nprox;             // persistent grid of the row kernel (blocks)
+};
+
+struct IterBufs {
+    void* X[2];
+    void* Xb;
+    double* p;         // p^k (committed)
+    double* pc;        // candidate p^{k+1}
+    float2* pff;       // candidate as float-float (MIXED)
+    double* pbar;
+    double* C[3];      // column sums c^{k-1}, c^k, c_new (roles in Ctl)
+    unsigned long long* acc;   // fixed-point accumulators (MIXED) or double bits (FP64)
+    double* t;         // s* of the last pass (per row)
+    double* part;      // per-block partials of the row kernel
+    double* part2;     // per-block partials of the dual kernel (2 per block)
+};
+
+int prox_blocks(bool mixed, int hot);  // persistent grid of the row kernel (occupancy based)
+int max_prox_blocks();                  // upper bound over all configurations
+void launch_price(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
+void launch_prox(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
+void launch_dual(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
+void launch_flush(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
+// one standalone prox pass with fixed tau and prices (no step control)
+void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* x_out, const double* p,
+                       double tau, unsigned long long* acc, double* t_out, double* c_out,
+                       double* part, Ctl* ctl, cudaStream_t s);
+
+struct KktBufs {
+    unsigned long long* acc;   // column-sum accumulator (MIXED fixed point / FP64 bits)
+    unsigned long long* M;     // column maxima of u_ij y_i (double bits)
+    double* c_out;             // column sums of x (may be null)
+    double* t_out;             // row utilities of x (may be null)
+    KktPart* part;             // per block
+    double* gpart;             // per block of the goods kernel (4 each)
+    KktOut* out;
+    Ctl* ctl;                  // ticket2
+    const void* xsel[2];       // when sel != null the point is xsel[*sel]
+    const int* sel;
+};
+int kkt_blocks();
+void launch_kkt(bool mixed, const DevMarket& mk, const void* x, const double* p, const KktBufs& kb,
+                cudaStream_t s);
+
+}  // namespace pdhcg

@@ -1,0 +1,159 @@
+// Preprocessing and helper kernels:
+//   - validation of the CSR market (Assumption 1: no empty row or column;
+//     u > 0 finite; w > 0 finite; strictly increasing columns within a row),
+//   - row scaling u_ij / max_j u_ij (Section 5, "Preprocessing"),
+//   - column degrees and relabelling of goods by decreasing degree,
+//   - the initial point x_ij = 1/deg_j (which clears the market),
+//   - restart helpers (copies, squared distances) and output gathers.
+#include "common.cuh"
+#include "prep.cuh"
+
+namespace pdhcg {
+
+__global__ void validate_kernel(int n, int m, long long nnz, const long long* __restrict__ rp,
+                                const int* __restrict__ col, const void* val, int val_f32,
+                                const double* __restrict__ w, unsigned int* err) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned int e = 0;
+    if (gw == 0 && lane == 0 && (rp[0] != 0 || rp[n] != nnz)) e |= ERR_ROWPTR;
+    for (long long i = gw; i < n; i += nw) {
+        const long long b = rp[i], en = rp[i + 1];
+        if (lane == 0) {
+            const double wi = w[i];
+            if (!(wi > 0.0) || !isfinite(wi)) e |= ERR_BUDGET;
+        }
+        if (en < b || b < 0 || en > nnz) { e |= ERR_ROWPTR; continue; }
+        if (en == b) { e |= ERR_EMPTY_ROW; continue; }
+        for (long long q = b + lane; q < en; q += 32) {
+            const int j = col[q];
+            if (j < 0 || j >= m) e |= ERR_COL_RANGE;
+            if (q > b && col[q - 1] >= j) e |= ERR_COL_ORDER;
+            const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
+            if (!(u > 0.0) || !isfinite(u)) e |= ERR_UTIL;
+        }
+    }
+    if (e) atomicOr(err, e);
+}
+
+__global__ void col_degree_kernel(long long nnz, const int* __restrict__ col, int m, int* deg) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x) {
+        const int j = col[q];
+        if (j >= 0 && j < m) atomicAdd(&deg[j], 1);
+    }
+}
+
+// row maximum, scaled utilities, relabelled goods, initial x
+template <typename V>
+__global__ void scale_kernel(int n, const long long* __restrict__ rp, const int* __restrict__ col, const void* val,
+                             int val_f32, const int* __restrict__ rank, const int* __restrict__ deg,
+                             double* __restrict__ rowmax, V* __restrict__ uv, int* __restrict__ cj,
+                             V* __restrict__ x0, int init_x) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = gw; i < n; i += nw) {
+        const long long b = rp[i], e = rp[i + 1];
+        double mx = 0.0;
+        for (long long q = b + lane; q < e; q += 32) {
+            const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
+            mx = fmax(mx, u);
+        }
+        mx = warp_max_d(mx);
+        if (lane == 0) rowmax[i] = mx;
+        for (long long q = b + lane; q < e; q += 32) {
+            const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
+            uv[q] = (V)(u / mx);
+            const int j = col[q];
+            cj[q] = rank[j];
+            if (init_x) x0[q] = (V)(1.0 / (double)deg[j]);
+        }
+    }
+}
+
+__global__ void fill_kernel(double* a, long long n, double v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) a[i] = v;
+}
+
+// internal (relabelled) <-> caller good order
+__global__ void gather_goods_kernel(int m, const int* __restrict__ rank, const double* __restrict__ src_int,
+                                    double* __restrict__ dst_orig) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) dst_orig[j] = src_int[rank[j]];
+}
+__global__ void scatter_goods_kernel(int m, const int* __restrict__ rank, const double* __restrict__ src_orig,
+                                     double* __restrict__ dst_int) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) dst_int[rank[j]] = src_orig[j];
+}
+__global__ void util_out_kernel(int n, const double* __restrict__ t, const double* __restrict__ rowmax, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = t[i] * rowmax[i];
+}
+template <typename Vs, typename Vd>
+__global__ void convert_kernel(long long n, const Vs* __restrict__ s, Vd* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) d[i] = (Vd)s[i];
+}
+
+// squared distance ||a - r||^2 accumulated in FP64 per block, then r <- a
+template <typename V>
+__global__ void dist_copy_kernel(long long n, const V* __restrict__ a, V* __restrict__ r, double* part) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = (double)a[i] - (double)r[i];
+        s = fma(d, d, s);
+        r[i] = a[i];
+    }
+    s = warp_sum_d(s);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+static int grid_for(long long n, int per = 256, int cap = 4096) {
+    long long b = (n + per - 1) / per;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+void k_validate(int n, int m, long long nnz, const long long* rp, const int* col, const void* val, int f32,
+                const double* w, unsigned int* err, cudaStream_t s) {
+    validate_kernel<<<grid_for((long long)n * 32, 256, 8192), 256, 0, s>>>(n, m, nnz, rp, col, val, f32, w, err);
+}
+void k_col_degree(long long nnz, const int* col, int m, int* deg, cudaStream_t s) {
+    col_degree_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, col, m, deg);
+}
+void k_scale(bool mixed, int n, const long long* rp, const int* col, const void* val, int f32, const int* rank,
+             const int* deg, double* rowmax, void* uv, int* cj, void* x0, int init_x, cudaStream_t s) {
+    int g = grid_for((long long)n * 32, 256, 8192);
+    if (mixed) scale_kernel<float><<<g, 256, 0, s>>>(n, rp, col, val, f32, rank, deg, rowmax, (float*)uv, cj, (float*)x0, init_x);
+    else scale_kernel<double><<<g, 256, 0, s>>>(n, rp, col, val, f32, rank, deg, rowmax, (double*)uv, cj, (double*)x0, init_x);
+}
+void k_fill(double* a, long long n, double v, cudaStream_t s) { fill_kernel<<<grid_for(n), 256, 0, s>>>(a, n, v); }
+void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, cudaStream_t s) {
+    gather_goods_kernel<<<grid_for(m), 256, 0, s>>>(m, rank, src_int, dst);
+}
+void k_scatter_goods(int m, const int* rank, const double* src, double* dst_int, cudaStream_t s) {
+    scatter_goods_kernel<<<grid_for(m), 256, 0, s>>>(m, rank, src, dst_int);
+}
+void k_util_out(int n, const double* t, const double* rowmax, double* out, cudaStream_t s) {
+    util_out_kernel<<<grid_for(n), 256, 0, s>>>(n, t, rowmax, out);
+}
+void k_convert(long long n, const void* src, bool src_f32, void* dst, bool dst_f32, cudaStream_t s) {
+    int g = grid_for(n);
+    if (src_f32 && dst_f32) cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, s);
+    else if (!src_f32 && !dst_f32) cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s);
+    else if (src_f32) convert_kernel<float, double><<<g, 256, 0, s>>>(n, (const float*)src, (double*)dst);
+    else convert_kernel<double, float><<<g, 256, 0, s>>>(n, (const double*)src, (float*)dst);
+}
+int dist_blocks() { return 1024; }
+void k_dist_copy(bool f32, long long n, const void* a, void* r, double* part, cudaStream_t s) {
+    if (f32) dist_copy_kernel<float><<<dist_blocks(), 256, 0, s>>>(n, (const float*)a, (float*)r, part);
+    else dist_copy_kernel<double><<<dist_blocks(), 256, 0, s>>>(n, (const double*)a, (double*)r, part);
+}
+
+}  // namespace pdhcg

@@ -1,0 +1,48 @@
+"""GPU Arrow-Debreu fixed point (Alg. 4) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import arrow
+from paper_2506_06258_gb300 import synth as S
+from tests.gpu_util import dev, host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    torch_cuda()
+    from paper_2506_06258_gb300 import api
+    s = api.Solver()
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_exchange_identity_endowments(solver, prec):
+    mk = S.config4(n=60, d_other=6, seed=500)
+    ref = arrow.ad_fixed_point(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, outer_tol=1e-9, inner_tol=1e-11)
+    tol = 1e-9 if prec == "fp64" else 1e-7
+    out = solver.ad_solve(dev(mk.row_ptr), dev(mk.col), dev(mk.val), dev(mk.w), mk.m, outer_tol=1e-7,
+                          tol=tol, precision=prec, max_outer=200)
+    assert out.status == 0, out.info
+    p = host(out.p)
+    assert np.max(np.abs(p - ref["p"]) / ref["p"]) <= 1e-5
+    assert np.max(np.abs(host(out.util) - p) / p) <= 1e-5      # w = p at the fixed point
+
+
+def test_general_endowments(solver):
+    rng = np.random.default_rng(4)
+    n, m = 30, 20
+    mk = S.bernoulli_market(n, m, 0.3, seed=41)
+    E = rng.uniform(0, 1, (n, m)) * (rng.uniform(size=(n, m)) < 0.5)
+    E[rng.integers(0, n, m), np.arange(m)] += 0.1
+    E /= E.sum(0, keepdims=True)
+    ref = arrow.ad_fixed_point(mk.row_ptr, mk.col, mk.val, np.ones(n), m, E=E, outer_tol=1e-9, inner_tol=1e-11)
+    er, ec = np.nonzero(E)
+    e_rp = np.concatenate(([0], np.cumsum(np.bincount(er, minlength=n)))).astype(np.int64)
+    out = solver.ad_solve(dev(mk.row_ptr), dev(mk.col), dev(mk.val), dev(np.ones(n)), m,
+                          E=(dev(e_rp), dev(ec.astype(np.int32)), dev(E[er, ec])), outer_tol=1e-8, tol=1e-9,
+                          precision="fp64")
+    assert out.status == 0
+    assert np.max(np.abs(host(out.p) - ref["p"]) / ref["p"]) <= 1e-5
