@@ -123,6 +123,9 @@ typedef struct pdhcg_handle_s* pdhcg_handle;
  * Library plumbing
  * ------------------------------------------------------------------------- */
 const char* pdhcg_status_string(pdhcg_status s);
+/* Text of the last CUDA error met by a library call on this host thread
+ * ("no error" if none); meant for diagnostics after PDHCG_ERR_CUDA. */
+const char* pdhcg_last_error(void);
 int32_t pdhcg_version(void);      /* major * 100 + minor */
 
 /* Defaults: tol 1e-6, max_iter 1e6, time limit 1e9 s, MIXED, check every 64,

@@ -49,6 +49,7 @@ _P = ctypes.POINTER
 _SIGS = {
     "pdhcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pdhcg_version": (c_int32, []),
+    "pdhcg_last_error": (ctypes.c_char_p, []),
     "pdhcg_default_params": (None, [_P(pdhcg_params)]),
     "pdhcg_create": (ctypes.c_int, [_P(c_void_p), c_void_p]),
     "pdhcg_destroy": (ctypes.c_int, [c_void_p]),
@@ -105,10 +106,15 @@ def status_string(st: int) -> str:
     return _fn("pdhcg_status_string")(st).decode()
 
 
+def last_error() -> str:
+    return _fn("pdhcg_last_error")().decode()
+
+
 class PdhcgError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = status
-        super().__init__(f"{where}: status {status} ({status_string(status)})")
+        extra = f"; CUDA: {last_error()}" if status == PDHCG_ERR_CUDA else ""
+        super().__init__(f"{where}: status {status} ({status_string(status)}){extra}")
 
 
 def default_params(**overrides) -> pdhcg_params:

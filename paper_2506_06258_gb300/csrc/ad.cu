@@ -51,14 +51,6 @@ __global__ void rescale_change_kernel(int n, double* __restrict__ a, double scal
 
 }  // namespace
 
-#define CK(x)                                                          \
-    do {                                                               \
-        cudaError_t e_ = (x);                                          \
-        if (e_ != cudaSuccess) {                                       \
-            if (e_ == cudaErrorMemoryAllocation) return PDHCG_ERR_OOM; \
-            return PDHCG_ERR_CUDA;                                     \
-        }                                                              \
-    } while (0)
 
 pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_t* e_row_ptr, const int32_t* e_col,
                             const double* e_val, double outer_tol, int32_t max_outer, const pdhcg_params* prm,
@@ -91,6 +83,7 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
         eval = (const double*)stage_in(h->ad_e_val, e_val, ennz * sizeof(double), s, &err);
         CK(err);
     }
+    h->tight_kappa = prm->tight_kappa;
     CK(ensure(h->ad_w, n * sizeof(double)));
     CK(ensure(h->ad_wn, n * sizeof(double)));
     CK(ensure(h->ad_p, m * sizeof(double)));

@@ -56,6 +56,7 @@ struct Ctl {
     unsigned int ticket2;  // last-block-done counter of the KKT goods kernel
     int row_cap;           // active-set rounds per row solve
     int pad;
+    unsigned long long work[kMaxBuckets];   // dynamic work counters of the row kernel
 };
 
 // Results of one KKT evaluation (written by the KKT goods kernel's last block).
@@ -211,6 +212,7 @@ struct DevMarket {
     int nb;
     int hot;               // goods [0, hot) accumulate in shared memory
     int nprox;             // persistent grid of the row kernel (blocks)
+    int mixed;             // value type of uv: 1 float, 0 double
 };
 
 struct IterBufs {
@@ -225,6 +227,8 @@ struct IterBufs {
     double* t;         // s* of the last pass (per row)
     double* part;      // per-block partials of the row kernel
     double* part2;     // per-block partials of the dual kernel (2 per block)
+    float2* pff_p;     // committed p and p-bar as float-float (for the MIXED KKT)
+    float2* pff_pb;
 };
 
 int prox_blocks(bool mixed, int hot);  // persistent grid of the row kernel (occupancy based)
@@ -232,6 +236,7 @@ int max_prox_blocks();                  // upper bound over all configurations
 void launch_price(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
 void launch_prox(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
 void launch_dual(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
+void launch_to_ff(int m, const double* p, float2* pff, cudaStream_t s);
 void launch_flush(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
 // one standalone prox pass with fixed tau and prices (no step control)
 void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* x_out, const double* p,
@@ -249,6 +254,8 @@ struct KktBufs {
     Ctl* ctl;                  // ticket2
     const void* xsel[2];       // when sel != null the point is xsel[*sel]
     const int* sel;
+    const float2* pff;         // MIXED: the prices as float-float
+    float* nd_part;            // MIXED: per-block max_ij (u_ij y_i - p_j)
 };
 int kkt_blocks();
 void launch_kkt(bool mixed, const DevMarket& mk, const void* x, const double* p, const KktBufs& kb,

@@ -12,311 +12,58 @@
 //                              dp^T K dx and ||dp||^2, and in its last block
 //                              applies the adaptive step rule (Section 5)
 //
-// Row solver.  phi(s) = s - sum_j u_j [a_j + c_j / s]_+ (a = x - tau p,
-// c = tau w u) is increasing (Section 2.2).  Freezing the active set S at the
-// current s turns the equation into s^2 - A s - C = 0 (A = sum_S u a,
-// C = sum_S u c); its positive root is a lower bound of s* (the frozen sum is a
-// minorant that touches at s), and iterating "active set -> root" climbs
-// monotonically to s*, ending when the active set no longer changes; the
-// result is then exact.  The rounds run in FP32 to find the active set; one
-// final float-float round evaluates A, C, s* and the new x with about 48 bits,
-// which the cancellation a_j + c_j/s (a_j can be much larger than x_j) needs.
-// This replaces the paper's 32-section search (a GPU design for H100) by an
-// exact finite procedure; the paper's searches remain in the oracle.
+// The row solver itself (rowsolve.cuh) replaces the paper's 32-section search
+// (a GPU design for H100) by an exact finite procedure; the paper's searches
+// remain in the oracle.
 #include "common.cuh"
+#include "rowsolve.cuh"
 
 namespace pdhcg {
 
 // ---------------------------------------------------------------------------
-// positive root of s^2 - A s - C = 0 (C >= 0), cancellation free
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float root32(float A, float C) {
-    float D = fmaf(A, A, 4.0f * C);
-    float sq = sqrtf(fmaxf(D, 0.0f));
-    return A >= 0.0f ? 0.5f * (A + sq) : (2.0f * C) / (sq - A);
-}
-__device__ __forceinline__ ff root_ff(ff A, ff C) {
-    ff D = ff_add(ff_mul(A, A), ff_mul_f(C, 4.0f));
-    ff sq = ff_sqrt(D);
-    if (A.hi >= 0.0f) return ff_mul_f(ff_add(A, sq), 0.5f);
-    return ff_div(ff_mul_f(C, 2.0f), ff_sub(sq, A));
-}
-__device__ __forceinline__ double root64(double A, double C) {
-    double D = fma(A, A, 4.0 * C);
-    double sq = sqrt(fmax(D, 0.0));
-    return A >= 0.0 ? 0.5 * (A + sq) : (2.0 * C) / (sq - A);
-}
-
-// ---------------------------------------------------------------------------
-// column-sum accumulation
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void acc_add_fixed(unsigned long long* s, unsigned long long* g, int hot, int j, float x) {
-    if (x > 0.0f) {
-        unsigned long long v = (unsigned long long)__float2ll_rn(x * kFixScaleF);
-        if (j < hot) atomicAdd(&s[j], v);
-        else atomicAdd(&g[j], v);
-    }
-}
-__device__ __forceinline__ void acc_add_f64(unsigned long long* s, unsigned long long* g, int hot, int j, double x) {
-    if (x > 0.0) {
-        if (j < hot) atomicAdd((double*)&s[j], x);
-        else atomicAdd((double*)&g[j], x);
-    }
-}
-
-struct RowCtx {
-    float tau_hi, tau_lo;
-    double tau;
-    float fold_w;
-    double fold_wd;
-    bool fold;
-    int cap;
-};
-
-// ---------------------------------------------------------------------------
-// MIXED row solve: G lanes per row, row data either in registers (LONG=false,
-// d <= G*kSlots) or streamed in chunks of 32*kSlots (LONG=true, G=32).
-// Every lane of the warp calls this together; `valid` marks real rows.
-// ---------------------------------------------------------------------------
-template <int G, bool LONG>
-__device__ void row_mixed(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
-                          float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
-                          unsigned long long* acc_s, unsigned long long* acc_g, double* __restrict__ t_out,
-                          const RowCtx& rc, int row, bool valid, float& dx2, int& capped) {
-    const int tl = (threadIdx.x & 31) & (G - 1);
-    const long long b = valid ? mk.rp[row] : 0;
-    const long long e = valid ? mk.rp[row + 1] : 0;
-    const ff tau = ff_make(rc.tau_hi, rc.tau_lo);
-    const double wi = valid ? mk.w[row] : 1.0;
-    const ff tw = ff_mul(tau, ff_from_double(wi));
-    const int span = G * kSlots;
-    const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
-
-    float ru[kSlots], rx[kSlots], rah[kSlots], ral[kSlots];
-    int rj[kSlots];
-    bool rin[kSlots];
-
-    auto load_chunk = [&](int c) {
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) {
-            long long idx = b + (long long)c * span + k * G + tl;
-            rin[k] = idx < e;
-            if (rin[k]) {
-                int j = __ldg(mk.cj + idx);
-                float u = __ldg(U + idx);
-                float x = Xin[idx];
-                float2 p = __ldg(pff + j);
-                ff a = ff_sub(ff_make(x, 0.0f), ff_mul(tau, ff_make(p.x, p.y)));
-                rj[k] = j; ru[k] = u; rx[k] = x; rah[k] = a.hi; ral[k] = a.lo;
-            } else {
-                rj[k] = 0; ru[k] = 0.0f; rx[k] = 0.0f; rah[k] = 0.0f; ral[k] = 0.0f;
-            }
-        }
-    };
-
-    // ---- starting point s0 = u^T x^k (Alg. 3's trial value) ----
-    float s0 = 0.0f, qall = 0.0f;
-    for (int c = 0; c < nch; c++) {
-        if (LONG || c == 0) load_chunk(c);
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) { s0 = fmaf(ru[k], rx[k], s0); qall = fmaf(ru[k], ru[k], qall); }
-    }
-    s0 = group_sum<G>(s0);
-    qall = group_sum<G>(qall);
-    if (!(s0 > 0.0f)) s0 = sqrtf(tw.hi * qall);   // all entries active: s^2 ~ C
-    if (!(s0 > 0.0f)) s0 = 1.0f;
-
-    // ---- FP32 active-set rounds ----
-    float s = s0, s_last = -1.0f;
-    bool gdone = !valid;
-    int rounds = 0;
-    while (__any_sync(0xffffffffu, !gdone)) {
-        const float R = tw.hi / s;
-        float A = 0.0f, Q = 0.0f;
-        for (int c = 0; c < nch; c++) {
-            if (LONG) load_chunk(c);
-#pragma unroll
-            for (int k = 0; k < kSlots; k++) {
-                if (rin[k] && fmaf(ru[k], R, rah[k]) > 0.0f) {
-                    A = fmaf(ru[k], rah[k], A);
-                    Q = fmaf(ru[k], ru[k], Q);
-                }
-            }
-        }
-        A = group_sum<G>(A);
-        Q = group_sum<G>(Q);
-        if (!gdone) {
-            float sn = root32(A, tw.hi * Q);
-            if (sn == s_last) {
-                gdone = true;                    // same root twice: the set is stable
-            } else {
-                s = (rounds == 0) ? sn : fmaxf(s, sn);
-                s_last = sn;
-                if (++rounds >= rc.cap) { gdone = true; if (tl == 0 && valid) capped++; }
-            }
-        }
-    }
-
-    // ---- float-float round(s): exact root for the active set, re-checked ----
-    float R32 = tw.hi / s;
-    ff sst = ff_make(s, 0.0f), Rff = ff_make(R32, 0.0f);
-    bool pdone = !valid;
-    for (int att = 0; att < 3; att++) {
-        ff A = ff_make(0.0f, 0.0f), Q = ff_make(0.0f, 0.0f);
-        for (int c = 0; c < nch; c++) {
-            if (LONG) load_chunk(c);
-#pragma unroll
-            for (int k = 0; k < kSlots; k++) {
-                bool act = rin[k] && (att == 0 ? fmaf(ru[k], R32, rah[k]) > 0.0f
-                                               : ff_pos(ff_add(ff_make(rah[k], ral[k]), ff_mul_f(Rff, ru[k]))));
-                if (act) {
-                    A = ff_add(A, ff_mul_f(ff_make(rah[k], ral[k]), ru[k]));
-                    Q = ff_add(Q, two_prod(ru[k], ru[k]));
-                }
-            }
-        }
-        A = group_sum<G>(A);
-        Q = group_sum<G>(Q);
-        ff sn = root_ff(A, ff_mul(tw, Q));
-        ff Rn = ff_div(tw, sn);
-        // does the active set at the new root agree with the one used?
-        bool changed = false;
-        for (int c = 0; c < nch; c++) {
-            if (LONG) load_chunk(c);
-#pragma unroll
-            for (int k = 0; k < kSlots; k++) {
-                if (!rin[k]) continue;
-                bool was = att == 0 ? fmaf(ru[k], R32, rah[k]) > 0.0f
-                                    : ff_pos(ff_add(ff_make(rah[k], ral[k]), ff_mul_f(Rff, ru[k])));
-                bool now = ff_pos(ff_add(ff_make(rah[k], ral[k]), ff_mul_f(Rn, ru[k])));
-                changed |= (was != now);
-            }
-        }
-        bool any_changed = group_any<G>(changed);
-        if (!pdone) { sst = sn; Rff = Rn; }
-        if (!any_changed) pdone = true;
-        if (!__any_sync(0xffffffffu, !pdone)) break;
-    }
-
-    // ---- new iterate, average fold, column sums ----
-    const float fw = rc.fold_w;
-    for (int c = 0; c < nch; c++) {
-        if (LONG) load_chunk(c);
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) {
-            if (!rin[k]) continue;
-            long long idx = b + (long long)c * span + k * G + tl;
-            ff v = ff_add(ff_make(rah[k], ral[k]), ff_mul_f(Rff, ru[k]));
-            float xn = v.hi > 0.0f ? v.hi : 0.0f;
-            Xout[idx] = xn;
-            float d = xn - rx[k];
-            dx2 = fmaf(d, d, dx2);
-            if (rc.fold) {
-                float xb = (fw == 1.0f) ? rx[k] : fmaf(fw, rx[k] - Xb[idx], Xb[idx]);
-                Xb[idx] = xb;
-            }
-            acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
-        }
-    }
-    if (valid && tl == 0) t_out[row] = ff_to_double(sst);
-}
-
-// ---------------------------------------------------------------------------
-// FP64 row solve (plain form): the same active-set iteration in double.
-// ---------------------------------------------------------------------------
-template <int G, bool LONG>
-__device__ void row_fp64(const DevMarket& mk, const double* __restrict__ U, const double* __restrict__ Xin,
-                         double* __restrict__ Xout, double* __restrict__ Xb, const double* __restrict__ pc,
-                         unsigned long long* acc_s, unsigned long long* acc_g, double* __restrict__ t_out,
-                         const RowCtx& rc, int row, bool valid, double& dx2, int& capped) {
-    const int tl = (threadIdx.x & 31) & (G - 1);
-    const long long b = valid ? mk.rp[row] : 0;
-    const long long e = valid ? mk.rp[row + 1] : 0;
-    const double wi = valid ? mk.w[row] : 1.0;
-    const double tw = rc.tau * wi;
-    const int span = G * kSlots;
-    const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
-    double ru[kSlots], rx[kSlots], ra[kSlots];
-    int rj[kSlots];
-    bool rin[kSlots];
-    auto load_chunk = [&](int c) {
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) {
-            long long idx = b + (long long)c * span + k * G + tl;
-            rin[k] = idx < e;
-            if (rin[k]) {
-                int j = __ldg(mk.cj + idx);
-                double u = __ldg(U + idx);
-                double x = Xin[idx];
-                rj[k] = j; ru[k] = u; rx[k] = x; ra[k] = x - rc.tau * __ldg(pc + j);
-            } else {
-                rj[k] = 0; ru[k] = 0.0; rx[k] = 0.0; ra[k] = 0.0;
-            }
-        }
-    };
-    double s0 = 0.0, qall = 0.0;
-    for (int c = 0; c < nch; c++) {
-        if (LONG || c == 0) load_chunk(c);
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) { s0 = fma(ru[k], rx[k], s0); qall = fma(ru[k], ru[k], qall); }
-    }
-    s0 = group_sum<G>(s0);
-    qall = group_sum<G>(qall);
-    if (!(s0 > 0.0)) s0 = sqrt(tw * qall);
-    if (!(s0 > 0.0)) s0 = 1.0;
-    double s = s0, s_last = -1.0;
-    bool gdone = !valid;
-    int rounds = 0;
-    while (__any_sync(0xffffffffu, !gdone)) {
-        const double R = tw / s;
-        double A = 0.0, Q = 0.0;
-        for (int c = 0; c < nch; c++) {
-            if (LONG) load_chunk(c);
-#pragma unroll
-            for (int k = 0; k < kSlots; k++) {
-                if (rin[k] && fma(ru[k], R, ra[k]) > 0.0) {
-                    A = fma(ru[k], ra[k], A);
-                    Q = fma(ru[k], ru[k], Q);
-                }
-            }
-        }
-        A = group_sum<G>(A);
-        Q = group_sum<G>(Q);
-        if (!gdone) {
-            double sn = root64(A, tw * Q);
-            if (sn == s_last) {
-                gdone = true;
-            } else {
-                s = (rounds == 0) ? sn : fmax(s, sn);
-                s_last = sn;
-                if (++rounds >= rc.cap) { gdone = true; if (tl == 0 && valid) capped++; }
-            }
-        }
-    }
-    const double R = tw / s;
-    const double fw = rc.fold_wd;
-    for (int c = 0; c < nch; c++) {
-        if (LONG) load_chunk(c);
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) {
-            if (!rin[k]) continue;
-            long long idx = b + (long long)c * span + k * G + tl;
-            double xn = fmax(fma(ru[k], R, ra[k]), 0.0);
-            Xout[idx] = xn;
-            double d = xn - rx[k];
-            dx2 = fma(d, d, dx2);
-            if (rc.fold) Xb[idx] = (fw == 1.0) ? rx[k] : fma(fw, rx[k] - Xb[idx], Xb[idx]);
-            acc_add_f64(acc_s, acc_g, mk.hot, rj[k], xn);
-        }
-    }
-    if (valid && tl == 0) t_out[row] = s;
-}
-
-// ---------------------------------------------------------------------------
 // the persistent row kernel
 // ---------------------------------------------------------------------------
+// One bucket of register-resident rows (MIXED): each warp takes chunks of
+// units from the bucket's counter; while one unit is solved the next unit's
+// (good id, utility, x^k) are already being loaded (software prefetch).
+template <int G>
+__device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned long long* counter, const void* Xin,
+                             void* Xout, const IterBufs& bf, const float2* sp, unsigned long long* acc_s,
+                             const RowCtx& rc, float& dxf, int& capped) {
+    constexpr int rpw = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const long long units = (bk.count + rpw - 1) / rpw;
+    const float* U = (const float*)mk.uv;
+    const float* Xi = (const float*)Xin;
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, 16ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= units) break;
+        const long long uend = min((long long)base + 16, units);
+        long long slot = (long long)base * rpw + lane / G;
+        bool vn = slot < bk.count;
+        int rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
+        RowRegs nx;
+        row_load<G>(mk, U, Xi, rn, vn, nx);
+        for (long long u = (long long)base; u < uend; u++) {
+            RowRegs cr = nx;
+            const int rc_row = rn;
+            const bool vc = vn;
+            if (u + 1 < uend) {
+                slot = (u + 1) * rpw + lane / G;
+                vn = slot < bk.count;
+                rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
+                row_load<G>(mk, U, Xi, rn, vn, nx);
+            }
+            row_mixed_core<G, false>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
+                                     rc_row, vc, dxf, capped, cr);
+        }
+    }
+}
+
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads) prox_kernel(DevMarket mk, const void* Xin_fixed, void* Xout_fixed,
+__global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const void* Xin_fixed, void* Xout_fixed,
                                                          IterBufs bf, Ctl* ctl, int fixed) {
     extern __shared__ unsigned long long acc_s[];
     if (!ctl->active) return;
@@ -331,13 +78,15 @@ __global__ void __launch_bounds__(kThreads) prox_kernel(DevMarket mk, const void
     const int cur = ctl->cur;
     const void* Xin = fixed ? Xin_fixed : (cur ? bf.X[1] : bf.X[0]);
     void* Xout = fixed ? Xout_fixed : (cur ? bf.X[0] : bf.X[1]);
-
-    for (int j = threadIdx.x; j < mk.hot; j += blockDim.x) acc_s[j] = 0ull;
+    // shared memory: column sums of the hot goods, then (MIXED) their prices
+    float2* sp = (float2*)(acc_s + mk.hot);
+    for (int j = threadIdx.x; j < mk.hot; j += blockDim.x) {
+        acc_s[j] = 0ull;
+        if (MIXED) sp[j] = bf.pff[j];
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const long long tw_ = (long long)gridDim.x * kWarps;
     float dxf = 0.0f;
     double dxd = 0.0;
     int capped = 0;
@@ -345,32 +94,46 @@ __global__ void __launch_bounds__(kThreads) prox_kernel(DevMarket mk, const void
     for (int bi = 0; bi < mk.nb; bi++) {
         const Bucket bk = mk.buckets[bi];
         const int g = bk.g;
+        if (MIXED && !bk.chunks) {
+            switch (g) {
+                case 4: bucket_mixed<4>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
+                case 8: bucket_mixed<8>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
+                case 16: bucket_mixed<16>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
+                default: bucket_mixed<32>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
+            }
+            continue;
+        }
         const int rpw = 32 / g;
         const long long units = (bk.count + rpw - 1) / rpw;
-        for (long long u = gw; u < units; u += tw_) {
-            long long slot = u * rpw + lane / g;
-            bool valid = slot < bk.count;
-            int row = valid ? mk.row_order[bk.first + slot] : 0;
-            if (MIXED) {
-                const float* U = (const float*)mk.uv;
-                float* Xo = (float*)Xout;
-                const float* Xi = (const float*)Xin;
-                float* Xb = (float*)bf.Xb;
-                if (bk.chunks) row_mixed<32, true>(mk, U, Xi, Xo, Xb, bf.pff, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped);
-                else if (g == 4) row_mixed<4, false>(mk, U, Xi, Xo, Xb, bf.pff, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped);
-                else if (g == 8) row_mixed<8, false>(mk, U, Xi, Xo, Xb, bf.pff, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped);
-                else if (g == 16) row_mixed<16, false>(mk, U, Xi, Xo, Xb, bf.pff, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped);
-                else row_mixed<32, false>(mk, U, Xi, Xo, Xb, bf.pff, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped);
-            } else {
-                const double* U = (const double*)mk.uv;
-                double* Xo = (double*)Xout;
-                const double* Xi = (const double*)Xin;
-                double* Xb = (double*)bf.Xb;
-                if (bk.chunks) row_fp64<32, true>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-                else if (g == 4) row_fp64<4, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-                else if (g == 8) row_fp64<8, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-                else if (g == 16) row_fp64<16, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-                else row_fp64<32, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+        const long long grab = bk.chunks ? 1 : 16;       // units taken per atomic
+        while (true) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctl->work[bi], (unsigned long long)grab);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((long long)base >= units) break;
+            const long long uend = min((long long)base + grab, units);
+            for (long long u = (long long)base; u < uend; u++) {
+                long long slot = u * rpw + lane / g;
+                bool valid = slot < bk.count;
+                int row = valid ? mk.row_order[bk.first + slot] : 0;
+                if (MIXED) {
+                    RowRegs R;
+                    R.b = valid ? mk.rp[row] : 0;
+                    R.e = valid ? mk.rp[row + 1] : 0;
+                    row_mixed_core<32, true>(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout,
+                                             (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf,
+                                             capped, R);
+                } else {
+                    const double* U = (const double*)mk.uv;
+                    double* Xo = (double*)Xout;
+                    const double* Xi = (const double*)Xin;
+                    double* Xb = (double*)bf.Xb;
+                    if (bk.chunks) row_fp64<32, true>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else if (g == 4) row_fp64<4, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else if (g == 8) row_fp64<8, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else if (g == 16) row_fp64<16, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else row_fp64<32, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                }
             }
         }
     }
@@ -406,6 +169,7 @@ __global__ void __launch_bounds__(kThreads) prox_kernel(DevMarket mk, const void
 template <bool MIXED>
 __global__ void price_kernel(DevMarket mk, IterBufs bf, Ctl* ctl) {
     if (!ctl->active) return;
+    if (blockIdx.x == 0 && threadIdx.x < kMaxBuckets) ctl->work[threadIdx.x] = 0ull;
     const bool pending = ctl->fold_pending;
     const double wgt = ctl->fold_wgt;
     const double sigma = ctl->sigma;
@@ -529,13 +293,22 @@ __global__ void flush_x_kernel(long long nnz, IterBufs bf, Ctl* ctl) {
     }
 }
 __global__ void flush_p_kernel(int m, IterBufs bf, Ctl* ctl) {
-    if (!ctl->fold_pending) return;
+    const bool pending = ctl->fold_pending;
     const double wgt = ctl->fold_wgt;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        double p = bf.pc[j];
-        bf.p[j] = p;
-        double pb = bf.pbar[j];
-        bf.pbar[j] = (wgt == 1.0) ? p : fma(wgt, p - pb, pb);
+        double p = bf.p[j], pb = bf.pbar[j];
+        if (pending) {
+            p = bf.pc[j];
+            bf.p[j] = p;
+            pb = (wgt == 1.0) ? p : fma(wgt, p - pb, pb);
+            bf.pbar[j] = pb;
+        }
+        if (bf.pff_p) {
+            float h = (float)p;
+            bf.pff_p[j] = make_float2(h, (float)(p - (double)h));
+            h = (float)pb;
+            bf.pff_pb[j] = make_float2(h, (float)(pb - (double)h));
+        }
     }
 }
 __global__ void flush_done_kernel(Ctl* ctl) { ctl->fold_pending = 0; }
@@ -543,7 +316,9 @@ __global__ void flush_done_kernel(Ctl* ctl) { ctl->fold_pending = 0; }
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static size_t prox_smem(const DevMarket& mk) { return (size_t)mk.hot * sizeof(unsigned long long); }
+// shared memory of the row kernel: hot column sums (8 B) and, MIXED, hot prices (8 B)
+static size_t prox_smem_bytes(bool mixed, int hot) { return (size_t)hot * (mixed ? 16 : 8); }
+static size_t prox_smem(const DevMarket& mk) { return prox_smem_bytes(mk.uv != nullptr && mk.mixed, mk.hot); }
 
 static void set_smem_attr() {
     static bool done = false;
@@ -568,7 +343,7 @@ static int sm_count() {
 int prox_blocks(bool mixed, int hot) {
     set_smem_attr();
     int per = 0;
-    size_t smem = (size_t)hot * sizeof(unsigned long long);
+    size_t smem = prox_smem_bytes(mixed, hot);
     if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prox_kernel<true>, kThreads, smem);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prox_kernel<false>, kThreads, smem);
     if (per < 1) per = 1;
@@ -617,6 +392,13 @@ __global__ void p_to_ff_kernel(int m, const double* p, float2* pff, double* pc) 
         pc[j] = v;
     }
 }
+__global__ void to_ff_kernel(int m, const double* p, float2* pff) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const double v = p[j];
+        const float h = (float)v;
+        pff[j] = make_float2(h, (float)(v - (double)h));
+    }
+}
 __global__ void cols_out_kernel(int m, bool mixed, unsigned long long* acc, double* c_out) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
         unsigned long long a = acc[j];
@@ -626,12 +408,17 @@ __global__ void cols_out_kernel(int m, bool mixed, unsigned long long* acc, doub
     }
 }
 __global__ void ctl_fixed_kernel(Ctl* ctl, double tau, int cap) {
+    for (int i = 0; i < kMaxBuckets; i++) ctl->work[i] = 0ull;
     ctl->active = 1;
     ctl->tau = tau;
     ctl->fold_pending = 0;
     ctl->cur = 0;
     ctl->row_cap = cap;
     ctl->capped = 0;
+}
+
+void launch_to_ff(int m, const double* p, float2* pff, cudaStream_t s) {
+    to_ff_kernel<<<vec_blocks(m), 256, 0, s>>>(m, p, pff);
 }
 
 void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* x_out, const double* p,

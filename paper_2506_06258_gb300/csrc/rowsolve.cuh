@@ -1,0 +1,360 @@
+// Row subproblem of Section 2.2 solved by G lanes of a warp (shared by the
+// single-market row kernel and the batched persistent kernel).
+//
+// FP64 form: phi(s) = s - sum_j u_j [a_j + c_j / s]_+ (a = x - tau p,
+// c = tau w u) is increasing.  Freezing the active set S at the current s turns
+// the equation into s^2 - A s - C = 0 (A = sum_S u a, C = sum_S u c); its
+// positive root is a lower bound of s* (the frozen sum is a minorant that
+// touches at s), and iterating "active set -> root" climbs monotonically to
+// s*, ending when the active set no longer changes, at which point the root is
+// exact.  MIXED form: safeguarded Newton on y = w/s with cancellation-free
+// residuals (see row_mixed).
+#pragma once
+#include "common.cuh"
+
+namespace pdhcg {
+
+// ---------------------------------------------------------------------------
+// positive root of s^2 - A s - C = 0 (C >= 0), cancellation free
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float root32(float A, float C) {
+    float D = fmaf(A, A, 4.0f * C);
+    float sq = sqrtf(fmaxf(D, 0.0f));
+    return A >= 0.0f ? 0.5f * (A + sq) : (2.0f * C) / (sq - A);
+}
+__device__ __forceinline__ ff root_ff(ff A, ff C) {
+    ff D = ff_add(ff_mul(A, A), ff_mul_f(C, 4.0f));
+    ff sq = ff_sqrt(D);
+    if (A.hi >= 0.0f) return ff_mul_f(ff_add(A, sq), 0.5f);
+    return ff_div(ff_mul_f(C, 2.0f), ff_sub(sq, A));
+}
+__device__ __forceinline__ double root64(double A, double C) {
+    double D = fma(A, A, 4.0 * C);
+    double sq = sqrt(fmax(D, 0.0));
+    return A >= 0.0 ? 0.5 * (A + sq) : (2.0 * C) / (sq - A);
+}
+
+// ---------------------------------------------------------------------------
+// column-sum accumulation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void acc_add_fixed(unsigned long long* s, unsigned long long* g, int hot, int j, float x) {
+    if (x > 0.0f) {
+        unsigned long long v = (unsigned long long)__float2ll_rn(x * kFixScaleF);
+        if (j < hot) atomicAdd(&s[j], v);
+        else atomicAdd(&g[j], v);
+    }
+}
+__device__ __forceinline__ void acc_add_f64(unsigned long long* s, unsigned long long* g, int hot, int j, double x) {
+    if (x > 0.0) {
+        if (j < hot) atomicAdd((double*)&s[j], x);
+        else atomicAdd((double*)&g[j], x);
+    }
+}
+
+struct RowCtx {
+    float tau_hi, tau_lo;
+    double tau;
+    float fold_w;
+    double fold_wd;
+    bool fold;
+    int cap;
+};
+
+// ---------------------------------------------------------------------------
+// MIXED row solve: G lanes per row, row data either in registers (LONG=false,
+// d <= G*kSlots) or streamed in chunks of 32*kSlots (LONG=true, G=32).
+// Every lane of the warp calls this together; `valid` marks real rows.
+//
+// Unknown y = w / s (the buyer's price of utility).  With d_j = p_j - u_j y the
+// row equation of Section 2.2 reads
+//     F(y) = sum_j u_j [x_j - tau d_j]_+ - w / y = 0,
+// F strictly increasing, F'(y) = tau sum_active u_j^2 + w / y^2 > 0.
+// The cancellation of the method sits in d_j (p_j and u_j y agree closely on
+// the support near equilibrium, and tau p_j can dwarf x_j), so p is carried in
+// float-float, y = y_h + y_l likewise, and
+//     d_j = fma(-u, y_l, fma(-u, y_h, p_h) + p_l)
+// is exact up to rounding relative to d_j itself; everything else is FP32.
+// Newton steps from y_0 = w / (u^T x^k) (the paper's trial value), safeguarded
+// by a bracket [lo, hi] on the sign of F, stop when |F| is at the FP32 noise
+// level of its two terms.
+// ---------------------------------------------------------------------------
+// Entries of one row held by one lane (register-resident rows).
+struct RowRegs {
+    long long b, e;
+    float u[kSlots], x[kSlots];
+    int j[kSlots];
+};
+
+template <int G>
+__device__ __forceinline__ void row_load(const DevMarket& mk, const float* __restrict__ U,
+                                         const float* __restrict__ Xin, int row, bool valid, RowRegs& R) {
+    const int tl = (threadIdx.x & 31) & (G - 1);
+    R.b = valid ? mk.rp[row] : 0;
+    R.e = valid ? mk.rp[row + 1] : 0;
+#pragma unroll
+    for (int k = 0; k < kSlots; k++) {
+        const long long idx = R.b + k * G + tl;
+        if (idx < R.e) {
+            R.j[k] = __ldg(mk.cj + idx);
+            R.u[k] = __ldg(U + idx);
+            R.x[k] = __ldcs(Xin + idx);
+        } else {
+            R.j[k] = -1;
+            R.u[k] = 0.0f;
+            R.x[k] = 0.0f;
+        }
+    }
+}
+
+// price of good j as float-float: hot goods from shared memory
+__device__ __forceinline__ float2 price_ff(const float2* __restrict__ pff, const float2* sp, int hot, int j) {
+    return j < hot ? sp[j] : __ldg(pff + j);
+}
+
+template <int G, bool LONG>
+__device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
+                               float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
+                               const float2* sp, unsigned long long* acc_s, unsigned long long* acc_g,
+                               double* __restrict__ t_out, const RowCtx& rc, int row, bool valid, float& dx2,
+                               int& capped, RowRegs& R) {
+    const int tl = (threadIdx.x & 31) & (G - 1);
+    const long long b = R.b;
+    const long long e = R.e;
+    const float tau = rc.tau_hi;
+    const double wd = valid ? mk.w[row] : 1.0;
+    const float wf = (float)wd;
+    const int span = G * kSlots;
+    const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
+
+    float rph[kSlots], rpl[kSlots], rxn[kSlots];
+    float* ru = R.u;
+    float* rx = R.x;
+    int* rj = R.j;
+
+    auto load_chunk = [&](int c) {
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            const long long idx = b + (long long)c * span + k * G + tl;
+            if (idx < e) {
+                rj[k] = __ldg(mk.cj + idx);
+                ru[k] = __ldg(U + idx);
+                rx[k] = Xin[idx];
+            } else {
+                rj[k] = -1; ru[k] = 0.0f; rx[k] = 0.0f;
+            }
+        }
+    };
+    auto gather_p = [&]() {
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            if (rj[k] >= 0) {
+                const float2 p = price_ff(pff, sp, mk.hot, rj[k]);
+                rph[k] = p.x;
+                rpl[k] = p.y;
+            } else {
+                rph[k] = 0.0f;
+                rpl[k] = 0.0f;
+            }
+        }
+    };
+    // residual terms at (yh, yl): R = sum u x_new, Q = sum_active u^2
+    auto eval_chunk = [&](float yh, float yl, float& Rs, float& Q) {
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            const float u = ru[k];
+            const float d = fmaf(-u, yl, fmaf(-u, yh, rph[k]) + rpl[k]);
+            float xn = fmaf(-tau, d, rx[k]);
+            xn = (rj[k] >= 0 && xn > 0.0f) ? xn : 0.0f;
+            rxn[k] = xn;
+            Rs = fmaf(u, xn, Rs);
+            if (xn > 0.0f) Q = fmaf(u, u, Q);
+        }
+    };
+
+    // ---- starting point: y_0 = w / (u^T x^k) ----
+    float s0 = 0.0f;
+    for (int c = 0; c < nch; c++) {
+        if (LONG) load_chunk(c);
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) s0 = fmaf(ru[k], rx[k], s0);
+    }
+    if (!LONG) gather_p();
+    s0 = group_sum<G>(s0);
+    float yh = (s0 > 0.0f) ? wf / s0 : 0.0f;
+    const bool need = !(yh > 0.0f) || !isfinite(yh);
+    if (__any_sync(0xffffffffu, need)) {
+        // x^k = 0 on this row: at y = max_j p_j / u_j every entry has d <= 0
+        float pmax_u = 0.0f;
+        for (int c = 0; c < nch; c++) {
+            if (LONG) { load_chunk(c); gather_p(); }
+#pragma unroll
+            for (int k = 0; k < kSlots; k++)
+                if (rj[k] >= 0) pmax_u = fmaxf(pmax_u, rph[k] / ru[k]);
+        }
+        for (int o = G / 2; o > 0; o >>= 1) pmax_u = fmaxf(pmax_u, __shfl_xor_sync(0xffffffffu, pmax_u, o));
+        if (need) yh = pmax_u > 0.0f ? pmax_u : 1.0f;
+    }
+    float yl = 0.0f, lo = 0.0f, hi = INFINITY, Rlast = 0.0f;
+    bool done = !valid;
+    int steps = 0;
+    while (__any_sync(0xffffffffu, !done)) {
+        float Rs = 0.0f, Q = 0.0f;
+        for (int c = 0; c < nch; c++) {
+            if (LONG) { load_chunk(c); gather_p(); }
+            eval_chunk(yh, yl, Rs, Q);
+        }
+        Rs = group_sum<G>(Rs);
+        Q = group_sum<G>(Q);
+        if (!done) {
+            Rlast = Rs;
+            const float ws = wf / yh;                       // w / y
+            const float F = Rs - ws;
+            if (fabsf(F) <= 4.8e-7f * (Rs + ws) || ++steps >= rc.cap) {
+                done = true;
+                if (steps >= rc.cap && tl == 0 && valid) capped++;
+            } else {
+                if (F > 0.0f) hi = yh; else lo = yh;
+                const float step = -F / fmaf(tau, Q, ws / yh);
+                ff yn = ff_add_f(ff_make(yh, yl), step);
+                if (!(yn.hi > lo && yn.hi < hi)) {          // Newton left the bracket
+                    const float mid = isinf(hi) ? 2.0f * yh : (lo > 0.0f ? 0.5f * (lo + hi) : 0.5f * hi);
+                    yn = ff_make(mid, 0.0f);
+                }
+                yh = yn.hi;
+                yl = yn.lo;
+            }
+        }
+    }
+
+    // ---- new iterate (last evaluation), average fold, column sums ----
+    const float fw = rc.fold_w;
+    for (int c = 0; c < nch; c++) {
+        if (LONG) {
+            load_chunk(c);
+            gather_p();
+            float Rs = 0.0f, Q = 0.0f;
+            eval_chunk(yh, yl, Rs, Q);
+        }
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            if (rj[k] < 0) continue;
+            const long long idx = b + (long long)c * span + k * G + tl;
+            const float xn = rxn[k];
+            __stcs(Xout + idx, xn);
+            const float d = xn - rx[k];
+            dx2 = fmaf(d, d, dx2);
+            if (rc.fold) Xb[idx] = (fw == 1.0f) ? rx[k] : fmaf(fw, rx[k] - Xb[idx], Xb[idx]);
+            acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
+        }
+    }
+    if (valid && tl == 0) t_out[row] = (double)Rlast;
+}
+
+// Convenience form (loads the row itself): used by the batched kernel.
+template <int G, bool LONG>
+__device__ void row_mixed(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
+                          float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
+                          unsigned long long* acc_s, unsigned long long* acc_g, double* __restrict__ t_out,
+                          const RowCtx& rc, int row, bool valid, float& dx2, int& capped) {
+    RowRegs R;
+    if (LONG) {
+        R.b = valid ? mk.rp[row] : 0;
+        R.e = valid ? mk.rp[row + 1] : 0;
+    } else {
+        row_load<G>(mk, U, Xin, row, valid, R);
+    }
+    row_mixed_core<G, LONG>(mk, U, Xin, Xout, Xb, pff, pff, acc_s, acc_g, t_out, rc, row, valid, dx2, capped, R);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 row solve (plain form): the same active-set iteration in double.
+// ---------------------------------------------------------------------------
+template <int G, bool LONG>
+__device__ void row_fp64(const DevMarket& mk, const double* __restrict__ U, const double* __restrict__ Xin,
+                         double* __restrict__ Xout, double* __restrict__ Xb, const double* __restrict__ pc,
+                         unsigned long long* acc_s, unsigned long long* acc_g, double* __restrict__ t_out,
+                         const RowCtx& rc, int row, bool valid, double& dx2, int& capped) {
+    const int tl = (threadIdx.x & 31) & (G - 1);
+    const long long b = valid ? mk.rp[row] : 0;
+    const long long e = valid ? mk.rp[row + 1] : 0;
+    const double wi = valid ? mk.w[row] : 1.0;
+    const double tw = rc.tau * wi;
+    const int span = G * kSlots;
+    const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
+    double ru[kSlots], rx[kSlots], ra[kSlots];
+    int rj[kSlots];
+    bool rin[kSlots];
+    auto load_chunk = [&](int c) {
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            long long idx = b + (long long)c * span + k * G + tl;
+            rin[k] = idx < e;
+            if (rin[k]) {
+                int j = __ldg(mk.cj + idx);
+                double u = __ldg(U + idx);
+                double x = Xin[idx];
+                rj[k] = j; ru[k] = u; rx[k] = x; ra[k] = x - rc.tau * __ldg(pc + j);
+            } else {
+                rj[k] = 0; ru[k] = 0.0; rx[k] = 0.0; ra[k] = 0.0;
+            }
+        }
+    };
+    double s0 = 0.0, qall = 0.0;
+    for (int c = 0; c < nch; c++) {
+        if (LONG || c == 0) load_chunk(c);
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) { s0 = fma(ru[k], rx[k], s0); qall = fma(ru[k], ru[k], qall); }
+    }
+    s0 = group_sum<G>(s0);
+    qall = group_sum<G>(qall);
+    if (!(s0 > 0.0)) s0 = sqrt(tw * qall);
+    if (!(s0 > 0.0)) s0 = 1.0;
+    double s = s0, s_last = -1.0;
+    bool gdone = !valid;
+    int rounds = 0;
+    while (__any_sync(0xffffffffu, !gdone)) {
+        const double R = tw / s;
+        double A = 0.0, Q = 0.0;
+        for (int c = 0; c < nch; c++) {
+            if (LONG) load_chunk(c);
+#pragma unroll
+            for (int k = 0; k < kSlots; k++) {
+                if (rin[k] && fma(ru[k], R, ra[k]) > 0.0) {
+                    A = fma(ru[k], ra[k], A);
+                    Q = fma(ru[k], ru[k], Q);
+                }
+            }
+        }
+        A = group_sum<G>(A);
+        Q = group_sum<G>(Q);
+        if (!gdone) {
+            double sn = root64(A, tw * Q);
+            if (sn == s_last) {
+                gdone = true;
+            } else {
+                s = (rounds == 0) ? sn : fmax(s, sn);
+                s_last = sn;
+                if (++rounds >= rc.cap) { gdone = true; if (tl == 0 && valid) capped++; }
+            }
+        }
+    }
+    const double R = tw / s;
+    const double fw = rc.fold_wd;
+    for (int c = 0; c < nch; c++) {
+        if (LONG) load_chunk(c);
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            if (!rin[k]) continue;
+            long long idx = b + (long long)c * span + k * G + tl;
+            double xn = fmax(fma(ru[k], R, ra[k]), 0.0);
+            Xout[idx] = xn;
+            double d = xn - rx[k];
+            dx2 = fma(d, d, dx2);
+            if (rc.fold) Xb[idx] = (fw == 1.0) ? rx[k] : fma(fw, rx[k] - Xb[idx], Xb[idx]);
+            acc_add_f64(acc_s, acc_g, mk.hot, rj[k], xn);
+        }
+    }
+    if (valid && tl == 0) t_out[row] = s;
+}
+
+}  // namespace pdhcg

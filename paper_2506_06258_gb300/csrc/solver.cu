@@ -30,6 +30,16 @@ using namespace pdhcg;
 // ---------------------------------------------------------------------------
 namespace pdhcg {
 
+static thread_local char g_last_error[512] = "no error";
+
+cudaError_t note_error(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        snprintf(g_last_error, sizeof(g_last_error), "%s (%s) in %s", cudaGetErrorString(e), cudaGetErrorName(e), what);
+        cudaGetLastError();   // clear a non-sticky error so the next call starts clean
+    }
+    return e;
+}
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return cudaSuccess;
@@ -118,14 +128,6 @@ static double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-#define CK(x)                                             \
-    do {                                                  \
-        cudaError_t e_ = (x);                             \
-        if (e_ != cudaSuccess) {                          \
-            if (e_ == cudaErrorMemoryAllocation) return PDHCG_ERR_OOM; \
-            return PDHCG_ERR_CUDA;                        \
-        }                                                 \
-    } while (0)
 
 // ---------------------------------------------------------------------------
 // preprocessing (step a0): validation, row scaling, relabelling, buckets
@@ -135,6 +137,7 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     if (!mk || mk->n <= 0 || mk->m <= 0 || mk->nnz <= 0 || !mk->row_ptr || !mk->col || !mk->val || !mk->w)
         return PDHCG_ERR_INVALID;
     Prepared& P = h->prep;
+    h->state.valid = false;          // the buffers of a saved equilibrium are about to be reused
     const int n = mk->n, m = mk->m;
     const long long nnz = mk->nnz;
     const bool f32 = mk->val_type == PDHCG_VAL_F32;
@@ -212,6 +215,7 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     D.m = m;
     D.nnz = nnz;
     D.nb = 0;
+    D.mixed = mixed ? 1 : 0;
     for (int b = 0; b < 5; b++) {
         if (!cnt[b]) continue;
         Bucket B;
@@ -239,7 +243,7 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     D.row_order = (const int*)h->row_order.p;
     // hot goods in shared memory: as many as fit, but flushing them (blocks x
     // hot atomics) must stay small against nnz
-    long long hot = std::min<long long>(m, 8192);
+    long long hot = std::min<long long>(m, mixed ? 4096 : 8192);
     long long lim = nnz / (8LL * prox_blocks(mixed, (int)hot));
     if (hot > lim) hot = lim;
     if (hot < 0) hot = 0;
@@ -280,6 +284,9 @@ static pdhcg_status alloc_iter(pdhcg_handle h) {
     CK(ensure(h->part, std::max(max_prox_blocks(), dist_blocks()) * sizeof(double)));
     CK(ensure(h->part2, 2 * 1024 * sizeof(double)));
     CK(ensure(h->kpart, kkt_blocks() * sizeof(KktPart)));
+    CK(ensure(h->ndpart, kkt_blocks() * sizeof(float)));
+    CK(ensure(h->pff_p, m * sizeof(float2)));
+    CK(ensure(h->pff_pb, m * sizeof(float2)));
     CK(ensure(h->gpart, 4 * 64 * sizeof(double)));
     CK(ensure(h->ctl, sizeof(Ctl)));
     CK(ensure(h->kout, 2 * sizeof(KktOut)));
@@ -306,6 +313,8 @@ static IterBufs iter_bufs(pdhcg_handle h) {
     b.t = (double*)h->t.p;
     b.part = (double*)h->part.p;
     b.part2 = (double*)h->part2.p;
+    b.pff_p = h->prep.mixed ? (float2*)h->pff_p.p : nullptr;
+    b.pff_pb = h->prep.mixed ? (float2*)h->pff_pb.p : nullptr;
     return b;
 }
 
@@ -319,6 +328,8 @@ static KktBufs kkt_bufs(pdhcg_handle h, double* c_out, double* t_out, int slot) 
     k.gpart = (double*)h->gpart.p;
     k.out = (KktOut*)h->kout.p + slot;
     k.ctl = (Ctl*)h->ctl.p;
+    k.nd_part = (float*)h->ndpart.p;
+    k.pff = slot == 0 ? (const float2*)h->pff_p.p : (const float2*)h->pff_pb.p;
     return k;
 }
 
@@ -371,7 +382,11 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
     CK(cudaMemcpyAsync(h->prs.p, h->p.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->Xr.p, h->X0.p, nnz * vb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(h->acc.p, 0, 3 * (size_t)m * sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(h->M.p, 0, m * sizeof(double), s));
+    CK(cudaMemsetAsync(h->M.p, mixed ? 0x7f : 0, m * sizeof(double), s));
+    if (mixed) {
+        launch_to_ff(m, (const double*)h->p.p, (float2*)h->pff_p.p, s);
+        launch_to_ff(m, (const double*)h->p.p, (float2*)h->pff_pb.p, s);
+    }
     Ctl c0 = {};
     c0.eta = eta0;
     c0.omega = S.omega0;
@@ -414,13 +429,13 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
     chunk_begin_kernel<<<1, 1, 0, s>>>(ctl);
     for (int q = 0; q < passes; q++) {
         launch_price(mixed, P.dm, bf, ctl, s);
-        if (timing) cudaEventRecord(S.ev[2 * q], s);
+        if (timing) cudaEventRecordWithFlags(S.ev[2 * q], s, cudaEventRecordExternal);
         launch_prox(mixed, P.dm, bf, ctl, s);
-        if (timing) cudaEventRecord(S.ev[2 * q + 1], s);
+        if (timing) cudaEventRecordWithFlags(S.ev[2 * q + 1], s, cudaEventRecordExternal);
         launch_dual(mixed, P.dm, bf, ctl, s);
     }
     launch_flush(mixed, P.dm, bf, ctl, s);
-    if (timing) cudaEventRecord(S.ev[2 * passes], s);
+    if (timing) cudaEventRecordWithFlags(S.ev[2 * passes], s, cudaEventRecordExternal);
     {
         KktBufs k0 = kkt_bufs(h, (double*)h->c_cur.p, (double*)h->t_cur.p, 0);
         k0.xsel[0] = h->X0.p;
@@ -430,7 +445,7 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
         KktBufs k1 = kkt_bufs(h, (double*)h->c_avg.p, (double*)h->t_avg.p, 1);
         launch_kkt(mixed, P.dm, h->Xb.p, (const double*)h->pbar.p, k1, s);
     }
-    if (timing) cudaEventRecord(S.ev[2 * passes + 1], s);
+    if (timing) cudaEventRecordWithFlags(S.ev[2 * passes + 1], s, cudaEventRecordExternal);
     cudaMemcpyAsync(h->host->kout, h->kout.p, 2 * sizeof(KktOut), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&h->host->ctl, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     cudaError_t ce = cudaStreamEndCapture(s, &S.graph);
@@ -485,12 +500,13 @@ pdhcg_status session_step(pdhcg_handle h, long long chunks) {
         if (S.n_ev) {
             float ms = 0.0f;
             for (int q = 0; q < passes; q++) {
-                cudaEventElapsedTime(&ms, S.ev[2 * q], S.ev[2 * q + 1]);
-                S.prox_ms += ms;
+                if (note_error(cudaEventElapsedTime(&ms, S.ev[2 * q], S.ev[2 * q + 1]), "event timing") == cudaSuccess)
+                    S.prox_ms += ms;
             }
             S.prox_launches += c.passes - passes_before;
-            cudaEventElapsedTime(&ms, S.ev[2 * passes], S.ev[2 * passes + 1]);
-            S.kkt_ms += ms;
+            if (note_error(cudaEventElapsedTime(&ms, S.ev[2 * passes], S.ev[2 * passes + 1]), "event timing") ==
+                cudaSuccess)
+                S.kkt_ms += ms;
         }
         const KktOut kcur = h->host->kout[0], kavg = h->host->kout[1];
         if (c.nan_flag || !(kcur.kkt == kcur.kkt)) {
@@ -506,7 +522,11 @@ pdhcg_status session_step(pdhcg_handle h, long long chunks) {
             fprintf(stderr, "[pdhcg] it %lld passes %lld kkt cur %.3e avg %.3e eta %.3e omega %.3e restarts %d\n",
                     c.iters, c.passes, kcur.kkt, kavg.kkt, c.eta, c.omega, S.restarts);
         if (kc <= prm.tol) { S.converged = true; S.status = PDHCG_OK; break; }
-        if (c.iters >= prm.max_iter) { S.status = PDHCG_ERR_NOT_CONVERGED; S.t_loop += now_ms() - t_loop0; return PDHCG_ERR_NOT_CONVERGED; }
+        if (c.iters >= prm.max_iter || c.passes >= 4 * prm.max_iter + 10000) {
+            S.status = PDHCG_ERR_NOT_CONVERGED;
+            S.t_loop += now_ms() - t_loop0;
+            return PDHCG_ERR_NOT_CONVERGED;
+        }
         if ((S.t_loop + now_ms() - t_loop0) * 1e-3 > prm.time_limit_s) { S.status = PDHCG_ERR_TIMEOUT; break; }
         const long long inner = c.iters - S.iters_at_restart;
         if (restart_decision(kc, S.kkt_rs, S.kkt_prev, inner, c.iters, prm)) {
@@ -611,6 +631,8 @@ const char* pdhcg_status_string(pdhcg_status s) {
 }
 
 int32_t pdhcg_version(void) { return PDHCG_VERSION_MAJOR * 100 + PDHCG_VERSION_MINOR; }
+
+const char* pdhcg_last_error(void) { return g_last_error; }
 
 void pdhcg_default_params(pdhcg_params* p) {
     if (!p) return;
@@ -754,6 +776,7 @@ pdhcg_status pdhcg_fisher_begin(pdhcg_handle h, const pdhcg_market* mk, const pd
         p0i = (const double*)h->p0i.p;
     }
     const double t_prep = now_ms() - t0;
+    h->tight_kappa = prm->tight_kappa;
     st = session_begin(h, *prm, p0i);
     h->sess.t_setup += t_prep;
     h->state.valid = false;
@@ -858,8 +881,9 @@ pdhcg_status pdhcg_kkt(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precision p
     CK(ensure(h->p0i, P.m * sizeof(double)));
     k_scatter_goods(P.m, (const int*)h->rank.p, pd, (double*)h->p0i.p, s);
     CK(cudaMemsetAsync(h->acc.p, 0, P.m * sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(h->M.p, 0, P.m * sizeof(double), s));
+    CK(cudaMemsetAsync(h->M.p, mixed ? 0x7f : 0, P.m * sizeof(double), s));
     CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), s));
+    if (mixed) launch_to_ff(P.m, (const double*)h->p0i.p, (float2*)h->pff_p.p, s);
     KktBufs kb = kkt_bufs(h, nullptr, nullptr, 0);
     launch_kkt(mixed, P.dm, xd, (const double*)h->p0i.p, kb, s);
     KktOut o;

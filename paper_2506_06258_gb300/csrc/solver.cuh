@@ -18,6 +18,17 @@ struct DevBuf {
 };
 
 cudaError_t ensure(DevBuf& b, size_t bytes);
+// remembers the last failing CUDA call for pdhcg_last_error()
+cudaError_t note_error(cudaError_t e, const char* what);
+
+#define CK(x)                                                          \
+    do {                                                               \
+        cudaError_t e_ = pdhcg::note_error((x), #x);                   \
+        if (e_ != cudaSuccess) {                                       \
+            if (e_ == cudaErrorMemoryAllocation) return PDHCG_ERR_OOM; \
+            return PDHCG_ERR_CUDA;                                     \
+        }                                                              \
+    } while (0)
 bool is_device_ptr(const void* p);
 const void* stage_in(DevBuf& buf, const void* src, size_t bytes, cudaStream_t s, cudaError_t* err);
 void* out_loc(DevBuf& buf, void* dst, size_t bytes, cudaError_t* err);
@@ -105,10 +116,17 @@ struct pdhcg_handle_s {
     // iterates
     pdhcg::DevBuf X0, X1, Xb, Xr;
     pdhcg::DevBuf p, pc, pff, pbar, prs, C0, C1, C2, c_cur, c_avg, M, acc, t, t_cur, t_avg;
-    pdhcg::DevBuf part, part2, kpart, gpart, ctl, kout;
+    pdhcg::DevBuf part, part2, kpart, gpart, ctl, kout, pff_p, pff_pb, ndpart;
     // extra buffers of the AD loop, the batched solver and the adjoint
     pdhcg::DevBuf ad_w, ad_wn, ad_p, ad_e_rp, ad_e_col, ad_e_val;
-    pdhcg::DevBuf bt[16];
+    pdhcg::DevBuf bt[24];
+    int bt_table_mixed[5] = {-1, -1, -1, -1, -1};   // autotuned lanes per row by degree class
+    int bt_table_fp64[5] = {-1, -1, -1, -1, -1};
+    int batch_B = 0;
+    int bt_N = 0, bt_M = 0;           // sizes of the last batched solve (for backward)
+    long long bt_NNZ = 0;
+    bool bt_mixed = true;
+    double tight_kappa = 1e-5;
     pdhcg::DevBuf adj[16];
     pdhcg::HostMirror* host = nullptr;
 
@@ -117,7 +135,7 @@ struct pdhcg_handle_s {
                                 &rp, &w, &err, &deg, &degint, &rank, &row_order, &cj, &uv, &rowmax, &p0i,
                                 &X0, &X1, &Xb, &Xr, &p, &pc, &pff, &pbar, &prs, &C0, &C1, &C2, &c_cur,
                                 &c_avg, &M, &acc, &t, &t_cur, &t_avg, &part, &part2, &kpart, &gpart, &ctl,
-                                &kout, &ad_w, &ad_wn, &ad_p, &ad_e_rp, &ad_e_col, &ad_e_val};
+                                &kout, &pff_p, &pff_pb, &ndpart, &ad_w, &ad_wn, &ad_p, &ad_e_rp, &ad_e_col, &ad_e_val};
         for (auto* b : all) b->release();
         for (auto& b : bt) b.release();
         for (auto& b : adj) b.release();
