@@ -15,10 +15,11 @@ with node weights h_j = r_j p_j, h_i = -g_i t_i, H_C = sum_C h, P_C = sum_C p:
                   -1 at the buyer), solved exactly by leaf peeling on a tree;
     df/du_ij    = lambda_e / u_ij on G, 0 elsewhere;
     df/dw_i     = g_i t_i / w_i + H_C / P_C.
-Arrow-Debreu with E = I (w = p at the normalised fixed point): with
-r~ = r - (r^T p / sum p) 1, solve mu = r~ + P_w^T mu (P_w^T mu = H_C(mu)/P_C
-per agent) by fixed-point iteration, then df/du = the Fisher derivative with
-r replaced by mu.
+Arrow-Debreu with E = I (w = p at a fixed point): mu = r~ + P_w^T mu
+(P_w^T mu = H_C(mu)/P_C per agent), reduced exactly to a system over the
+tight-graph components (see ad_backward); df/du = the Fisher derivative with
+r replaced by mu.  Money is conserved per closed class of components, so the
+derivative holds each class's money fixed.
 """
 from __future__ import annotations
 
@@ -127,24 +128,47 @@ def ad_backward(row_ptr, col, val, x, p, t, r, kappa=1e-7):
     point w = p.  With pi_j = p_j / P_C and A mapping agent i to the component
     of buyer i, P_w^T mu = A^T lambda with lambda_C = sum_{j in C} pi_j mu_j, so
     mu = r~ + A^T lambda and lambda solves the K x K system
-        (I - Q) lambda = rho,  Q[C, C'] = sum_{j in C, C(buyer j) = C'} pi_j,
-        rho_C = sum_{j in C} pi_j r~_j,
-    singular along constants (Q is row-stochastic) and consistent because
-    p^T r~ = 0; it is solved by least squares."""
+        (I - Q) lambda = rho,  Q[C, C'] = sum_{j in C, cb(j) = C'} pi_j,
+        rho_C = sum_{j in C} pi_j r~_j.
+    Q is row-stochastic and every component is recurrent (money is conserved
+    per component), so its closed classes are the weakly connected classes of
+    the component graph C(good j) - C(buyer j).  Each class keeps its own money
+    at a fixed point, so the fixed point is unique only up to the split of money
+    between classes; the derivative holds every class's money fixed:
+    r~_j = r_j - (sum_class r p / sum_class p), which makes the system
+    consistent.  It is solved by least squares."""
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     col = np.asarray(col, dtype=np.int64)
     n = len(row_ptr) - 1
     m = len(p)
     p = np.asarray(p, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64)
-    S = p.sum()
-    rt = r - (r @ p / S)
     idx, ei, ej = tight_graph(row_ptr, col, val, p, x, p, t, kappa)
     comp = _components(n, m, ei, ej)
     labels = {c: k for k, c in enumerate(sorted(set(comp.tolist())))}
     K = len(labels)
     cb = np.array([labels[comp[i]] for i in range(n)])          # component of buyer i
     cg = np.array([labels[comp[n + j]] for j in range(m)])      # component of good j
+    # closed classes: weakly connected classes of the edges cg(j) - cb(j)
+    parent = list(range(K))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    for j in range(m):
+        a_, b_ = find(int(cg[j])), find(int(cb[j]))
+        if a_ != b_:
+            parent[a_] = b_
+    cls = np.array([find(c) for c in range(K)])
+    gcls = cls[cg]
+    rp_cls = defaultdict(float)
+    p_cls = defaultdict(float)
+    for j in range(m):
+        rp_cls[gcls[j]] += r[j] * p[j]
+        p_cls[gcls[j]] += p[j]
+    rt = np.array([r[j] - rp_cls[gcls[j]] / p_cls[gcls[j]] for j in range(m)])
     P = np.bincount(cg, weights=p, minlength=K)
     pi = p / P[cg]
     Q = np.zeros((K, K))
@@ -152,8 +176,8 @@ def ad_backward(row_ptr, col, val, x, p, t, r, kappa=1e-7):
     rho = np.bincount(cg, weights=pi * rt, minlength=K)
     lam = np.linalg.lstsq(np.eye(K) - Q, rho, rcond=None)[0]
     mu = rt + lam[cb]
-    mu -= (mu @ p) / S
     gu, _, info = fisher_backward(row_ptr, col, val, p, x, p, t, mu, None, kappa)
     info["ad_components"] = K
+    info["ad_classes"] = len(set(cls.tolist()))
     info["ad_residual"] = float(np.max(np.abs((np.eye(K) - Q) @ lam - rho)))
     return gu, mu, info

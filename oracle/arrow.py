@@ -20,10 +20,10 @@ from . import fisher as F
 
 
 def ad_fixed_point(row_ptr, col, val, w0, m, E=None, outer_tol=1e-6, max_outer=200, inner_tol=1e-10,
-                   inner_max_iter=400000):
+                   inner_max_iter=400000, x0=None, p0=None):
     w = np.asarray(w0, dtype=np.float64).copy()
     sum0 = w.sum()
-    x = p = None
+    x, p = x0, p0
     hist = []
     res = None
     for k in range(1, max_outer + 1):

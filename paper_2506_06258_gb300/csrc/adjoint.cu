@@ -16,13 +16,16 @@
 // unique.  Then df/du_e = lambda_e / u_e on G (0 elsewhere) and
 // df/dw_i = g_i t_i / w_i + H_C / P_C.
 //
-// Arrow-Debreu with E = I (w = p at the normalised fixed point): with
-// r~ = r - (r^T p / sum p) 1 and the component maps cg (good -> C) and
-// cb (buyer -> C), lambda in R^K solves (I - Q) lambda = rho,
-// Q[C, C'] = sum_{j in C, cb(j) = C'} pi_j, rho_C = sum_{j in C} pi_j r~_j;
-// Q is row-stochastic with left Perron vector P, so the damped iteration
-// lambda <- lambda/2 + (rho + Q lambda)/2 projected on P^T lambda = 0
-// converges; mu = r~ + lambda[cb] replaces r in the Fisher derivative.
+// Arrow-Debreu with E = I (w = p at a fixed point): with the component maps
+// cg (good -> C) and cb (buyer -> C), lambda in R^K solves (I - Q) lambda = rho,
+// Q[C, C'] = sum_{j in C, cb(j) = C'} pi_j, rho_C = sum_{j in C} pi_j r~_j.
+// Q is row-stochastic and every component is recurrent (money is conserved per
+// component), so the closed classes of Q are the weakly connected classes of
+// the edges cg(j) - cb(j); each class keeps its own money at a fixed point, so
+// the derivative holds it fixed: r~_j = r_j - (sum_class r p / sum_class p).
+// The damped iteration lambda <- (lambda + rho + Q lambda) / 2, projected per
+// class on sum_class P lambda = 0, converges; mu = r~ + lambda[cb] replaces r
+// in the Fisher derivative.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -237,6 +240,54 @@ __global__ void grad_w_kernel(int n, const int* label, const double* g, const do
 }
 
 // ---- Arrow-Debreu component system ----
+// classes of components: hook the agent edges C(good j) - C(buyer of agent j)
+__global__ void class_hook_kernel(int m, int n, const int* label, const int* agent_row, int* cl, int* changed) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const int a = cl[label[n + j]], b = cl[label[agent_row[j]]];
+        if (a == b) continue;
+        atomicMin(&cl[max(a, b)], min(a, b));
+        *changed = 1;
+    }
+}
+// per-class sums of r_j p_j and p_j, then r~_j = r_j - RP/PP of its class
+__global__ void class_sums_kernel(int m, int n, const int* label, const int* cl, const double* r, const double* p,
+                                  double* RP, double* PP) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const int c = cl[label[n + j]];
+        atomicAdd(&RP[c], r[j] * p[j]);
+        atomicAdd(&PP[c], p[j]);
+    }
+}
+__global__ void class_center_kernel(int m, int n, const int* label, const int* cl, const double* r, const double* RP,
+                                    const double* PP, double* rt) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const int c = cl[label[n + j]];
+        rt[j] = r[j] - RP[c] / PP[c];
+    }
+}
+// one damped step over component roots v: lam'_v = (lam_v + rho_v + (Q lam)_v) / 2,
+// accumulating per-class sums of P_v lam'_v for the projection
+__global__ void ad_step_kernel(int nv, const int* label, const int* cl, const double* P, const double* rho,
+                               const double* qlam, const double* lam, double* lam_new, double* csum) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+        if (label[v] != v) continue;
+        const double nl = 0.5 * (lam[v] + rho[v] + qlam[v]);
+        lam_new[v] = nl;
+        atomicAdd(&csum[cl[v]], P[v] * nl);
+    }
+}
+// projection per class and the largest change (as bits of a non-negative double)
+__global__ void ad_project_kernel(int nv, const int* label, const int* cl, const double* PPc, const double* csum,
+                                  double* lam_new, const double* lam, unsigned long long* dmax) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+        if (label[v] != v) continue;
+        const int c = cl[v];
+        const double nl = lam_new[v] - csum[c] / PPc[c];
+        lam_new[v] = nl;
+        const double d = fabs(nl - lam[v]);
+        if (d > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(d));
+    }
+}
 __global__ void ad_pi_kernel(int n, int m, const int* label, const double* p, const double* P, const double* rt,
                              double* rho, double* pi) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
@@ -271,11 +322,6 @@ int gsz(long long n) {
     return (int)std::max<long long>(1, std::min<long long>(b, 4096));
 }
 
-double host_sum(const std::vector<double>& v) {
-    double s = 0.0;
-    for (double x : v) s += x;
-    return s;
-}
 
 // Fisher derivative core on one (possibly block-diagonal) market.
 // r, g in the derivative's good / row space; outputs grad_u (entry order of a.cj)
@@ -496,74 +542,89 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
     a.kappa = h->tight_kappa;
     if (st.kind == 1) {
         // ---- Arrow-Debreu: replace r by mu (see the file comment) ----
-        double* rt = (double*)B[13].p;                 // r~ (internal good order)
-        double* pi = rt + m;
-        double* lam = pi + m;                          // indexed by label (node ids)
-        double* tmp = lam + (n + m);
-        double* mu = tmp + (n + m);
-        (void)mu;
-        // r~ = r - (r.p / sum p)
+        const int nv = n + m;
+        CK(ensure(B[13], 8 * (size_t)nv * sizeof(double)));
         CK(ensure(B[14], 64));
-        double* d2 = (double*)B[14].p;
-        CK(cudaMemsetAsync(d2, 0, 16, s));
-        dot2_kernel<<<gsz(m), 256, 0, s>>>(m, r_int, R.p, d2);
-        double hd[2];
-        CK(cudaMemcpyAsync(hd, d2, 16, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        CK(cudaMemcpyAsync(rt, r_int, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        axpy_const_kernel<<<gsz(m), 256, 0, s>>>(m, rt, -hd[0] / hd[1]);
-        // components of the tight graph (a first derivative pass with r~ gives them)
+        CK(ensure(B[15], m * sizeof(int)));
+        CK(ensure(B[16], (size_t)nv * sizeof(int)));
+        double* base = (double*)B[13].p;
+        double* rt = base;                        // [m]
+        double* pi = base + nv;                   // [m]
+        double* rho = base + 2 * (size_t)nv;      // by component root
+        double* lam = base + 3 * (size_t)nv;
+        double* lamn = base + 4 * (size_t)nv;
+        double* qlam = base + 5 * (size_t)nv;
+        double* csum = base + 6 * (size_t)nv;     // by class root
+        double* PPc = base + 7 * (size_t)nv;      // by class root (also RP during centring)
+        unsigned long long* dmax = (unsigned long long*)B[14].p;
+        int* changed = (int*)((char*)B[14].p + 8);
+        int* cl = (int*)B[16].p;
+        // components of the tight graph (one derivative pass computes them)
         double res0;
         int ne0, kc0;
-        pdhcg_status r0 = adjoint_core(h, a, rt, nullptr, gu, gw, 1, &res0, &ne0, &kc0, nullptr);
+        pdhcg_status r0 = adjoint_core(h, a, r_int, nullptr, gu, gw, 1, &res0, &ne0, &kc0, nullptr);
         if (r0 != PDHCG_OK && r0 != PDHCG_ERR_NOT_CONVERGED) return r0;
         const int* label = (const int*)h->adj[4].p;
-        const double* Pc = (const double*)h->adj[5].p + (n + m);
-        // agent j's buyer row (agent j = caller good j = caller row j, E = I)
-        CK(ensure(B[15], m * sizeof(int)));
+        const double* Pc = (const double*)h->adj[5].p + nv;
         {
             std::vector<int> agent_row(m);
             for (int j = 0; j < m; j++) agent_row[P.rank[j]] = j;     // internal good -> caller row
             CK(cudaMemcpyAsync(B[15].p, agent_row.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
         }
         const int* agent_row = (const int*)B[15].p;
-        double* rho = tmp;
-        CK(cudaMemsetAsync(rho, 0, (n + m) * sizeof(double), s));
-        CK(cudaMemsetAsync(lam, 0, (n + m) * sizeof(double), s));
-        ad_pi_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, R.p, Pc, rt, rho, pi);
-        // damped, projected iteration lambda <- (lambda + rho + Q lambda) / 2
-        std::vector<double> lam_h(n + m), q_h(n + m), rho_h(n + m), P_h(n + m);
-        CK(cudaMemcpyAsync(rho_h.data(), rho, (n + m) * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(P_h.data(), Pc, (n + m) * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const double Ptot = host_sum(P_h);
-        for (int it = 0; it < 20000; it++) {
-            CK(cudaMemsetAsync(tmp, 0, (n + m) * sizeof(double), s));
-            ad_q_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, agent_row, pi, lam, tmp);
-            CK(cudaMemcpyAsync(q_h.data(), tmp, (n + m) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        // closed classes of components
+        label_init_kernel<<<gsz(nv), 256, 0, s>>>(nv, cl);
+        for (int round = 0; round < 200; round++) {
+            CK(cudaMemsetAsync(changed, 0, 4, s));
+            class_hook_kernel<<<gsz(m), 256, 0, s>>>(m, n, label, agent_row, cl, changed);
+            for (int jmp = 0; jmp < 4; jmp++) jump_kernel<<<gsz(nv), 256, 0, s>>>(nv, cl, changed);
+            int ch = 0;
+            CK(cudaMemcpyAsync(&ch, changed, 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            double proj = 0.0, delta = 0.0, scale = 0.0;
-            std::vector<double> nl(n + m);
-            for (int c = 0; c < n + m; c++) nl[c] = 0.5 * (lam_h[c] + rho_h[c] + q_h[c]);
-            for (int c = 0; c < n + m; c++) proj += P_h[c] * nl[c];
-            proj /= Ptot;
-            for (int c = 0; c < n + m; c++) {
-                nl[c] -= proj;
-                delta = std::max(delta, std::fabs(nl[c] - lam_h[c]));
-                scale = std::max(scale, std::fabs(nl[c]));
-            }
-            lam_h.swap(nl);
-            CK(cudaMemcpyAsync(lam, lam_h.data(), (n + m) * sizeof(double), cudaMemcpyHostToDevice, s));
-            if (delta <= 1e-13 * std::max(1.0, scale)) break;
+            if (!ch) break;
+            if (round == 199) return PDHCG_ERR_NUMERIC;
         }
-        double* mu_d = tmp;
-        ad_mu_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, agent_row, rt, lam, mu_d);
-        CK(cudaMemsetAsync(d2, 0, 16, s));
-        dot2_kernel<<<gsz(m), 256, 0, s>>>(m, mu_d, R.p, d2);
-        CK(cudaMemcpyAsync(hd, d2, 16, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        axpy_const_kernel<<<gsz(m), 256, 0, s>>>(m, mu_d, -hd[0] / hd[1]);
-        CK(cudaMemcpyAsync(r_int, mu_d, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        // r~ = r - per-class (r.p / sum p)
+        CK(cudaMemsetAsync(csum, 0, 2 * (size_t)nv * sizeof(double), s));
+        class_sums_kernel<<<gsz(m), 256, 0, s>>>(m, n, label, cl, r_int, R.p, csum, PPc);
+        class_center_kernel<<<gsz(m), 256, 0, s>>>(m, n, label, cl, r_int, csum, PPc, rt);
+        // rho, pi; P per class for the projection
+        CK(cudaMemsetAsync(rho, 0, (size_t)nv * sizeof(double), s));
+        CK(cudaMemsetAsync(lam, 0, (size_t)nv * sizeof(double), s));
+        CK(cudaMemsetAsync(PPc, 0, (size_t)nv * sizeof(double), s));
+        ad_pi_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, R.p, Pc, rt, rho, pi);
+        class_sums_kernel<<<gsz(m), 256, 0, s>>>(m, n, label, cl, r_int, R.p, csum, PPc);   // PPc = class price totals
+        // damped, projected iteration, 16 steps per captured graph
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(dmax, 0, 8, s);
+        for (int k = 0; k < 16; k++) {
+            cudaMemsetAsync(qlam, 0, (size_t)nv * sizeof(double), s);
+            cudaMemsetAsync(csum, 0, (size_t)nv * sizeof(double), s);
+            ad_q_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, agent_row, pi, lam, qlam);
+            ad_step_kernel<<<gsz(nv), 256, 0, s>>>(nv, label, cl, Pc, rho, qlam, lam, lamn, csum);
+            if (k == 15) cudaMemsetAsync(dmax, 0, 8, s);
+            ad_project_kernel<<<gsz(nv), 256, 0, s>>>(nv, label, cl, PPc, csum, lamn, lam, dmax);
+            cudaMemcpyAsync(lam, lamn, (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        }
+        cudaMemcpyAsync(&h->host->kout[0], dmax, 8, cudaMemcpyDeviceToHost, s);
+        CK(cudaStreamEndCapture(s, &graph));
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+        bool ok = false;
+        for (int it = 0; it < 40000; it += 16) {
+            cudaError_t ce = cudaGraphLaunch(exec, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (note_error(ce, "adjoint fixed point") != cudaSuccess) break;
+            double d;
+            memcpy(&d, &h->host->kout[0], 8);
+            if (!(d > 1e-14)) { ok = true; break; }
+        }
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (!ok) return PDHCG_ERR_NOT_CONVERGED;
+        ad_mu_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, agent_row, rt, lam, r_int);
+        CK(cudaGetLastError());
     }
     double res;
     int ne, kc;

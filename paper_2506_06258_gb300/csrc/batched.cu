@@ -83,7 +83,7 @@ __device__ __forceinline__ void cas_max_pos(unsigned long long* a, double v) {
     const unsigned long long nv = dbits(v);
     unsigned long long old = *((volatile unsigned long long*)a);
     while (nv > old) {
-        const unsigned long long prev = atomicCAS(a, old, nv);
+        const unsigned long long prev = shared_cas_b64(a, old, nv);
         if (prev == old) break;
         old = prev;
     }
@@ -151,16 +151,16 @@ __global__ void batch_prep_kernel(BatchArgs a) {
             if (q > q0 && a.col[q - 1] >= j) e |= ERR_COL_ORDER;
             const double u = a.val_f32 ? (double)((const float*)a.val)[q] : ((const double*)a.val)[q];
             if (!(u > 0.0) || !isfinite(u)) e |= ERR_UTIL;
-            atomicAdd(&sdeg[j], 1);
+            shared_add_s32(&sdeg[j], 1);
         }
     }
-    if (e) atomicOr((unsigned int*)&err, e);
+    if (e) shared_or_b32((unsigned int*)&err, e);
     __syncthreads();
     double inv = 0.0, mx = 0.0;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         const int d = sdeg[j];
         a.deg[g0 + j] = d;
-        if (d == 0) atomicOr((unsigned int*)&err, ERR_EMPTY_COL);
+        if (d == 0) shared_or_b32((unsigned int*)&err, ERR_EMPTY_COL);
         else inv += 1.0 / (double)d;
         mx = fmax(mx, (double)d);
     }
@@ -234,8 +234,8 @@ __device__ void kkt_market(const BatchArgs& a, long long r0, long long r1, long 
             mxg = fmax(mxg, x * g);
             cas_max_pos(&Mx[j], uy);
             if (x > 0.0) {
-                if (MIXED) atomicAdd(&acc[j], (unsigned long long)__double2ll_rn(x * kFixScale));
-                else atomicAdd((double*)&acc[j], x);
+                if (MIXED) shared_add_u64(&acc[j], (unsigned long long)__double2ll_rn(x * kFixScale));
+                else shared_add_f64(&acc[j], x);
             }
         }
     }

@@ -148,6 +148,33 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
 __device__ __forceinline__ bool ff_pos(ff a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
 
 // ---------------------------------------------------------------------------
+// shared-memory atomics with the state space spelled out (a generic-address
+// atomic that resolves to shared memory is not supported for every operation)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void shared_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(smem_addr(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void shared_add_f64(void* p, double v) {
+    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(smem_addr(p)), "d"(v) : "memory");
+}
+__device__ __forceinline__ void shared_add_s32(int* p, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void shared_or_b32(unsigned* p, unsigned v) {
+    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void shared_min_s32(int* p, int v) {
+    asm volatile("red.shared.min.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long shared_cas_b64(unsigned long long* p, unsigned long long cmp,
+                                                            unsigned long long val) {
+    unsigned long long old;
+    asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "r"(smem_addr(p)), "l"(cmp), "l"(val) : "memory");
+    return old;
+}
+
+// ---------------------------------------------------------------------------
 // misc device helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double d) { return (unsigned long long)__double_as_longlong(d); }

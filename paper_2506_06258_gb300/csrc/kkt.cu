@@ -53,10 +53,10 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_kernel(DevMarket mk, const 
             if (x > 0.0) {
                 if (MIXED) {
                     unsigned long long v = (unsigned long long)__double2ll_rn(x * kFixScale);
-                    if (j < mk.hot) atomicAdd(&acc_s[j], v);
+                    if (j < mk.hot) shared_add_u64(&acc_s[j], v);
                     else atomicAdd(&kb.acc[j], v);
                 } else {
-                    if (j < mk.hot) atomicAdd((double*)&acc_s[j], x);
+                    if (j < mk.hot) shared_add_f64(&acc_s[j], x);
                     else atomicAdd((double*)&kb.acc[j], x);
                 }
             }
@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_mixed_kernel(DevMarket mk, 
             mnd = fmaxf(mnd, -d);
             const int key = fkey(d);
             if (j < mk.hot) {
-                if (key < dmin_s[j]) atomicMin(&dmin_s[j], key);
-                if (x > 0.0f) atomicAdd(&acc_s[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));
+                if (key < dmin_s[j]) shared_min_s32(&dmin_s[j], key);
+                if (x > 0.0f) shared_add_u64(&acc_s[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));
             } else {
                 if (key < ((volatile int*)dmin_g)[j]) atomicMin(&dmin_g[j], key);
                 if (x > 0.0f) atomicAdd(&kb.acc[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));

@@ -37,16 +37,17 @@ __device__ __forceinline__ double root64(double A, double C) {
 // ---------------------------------------------------------------------------
 // column-sum accumulation
 // ---------------------------------------------------------------------------
+// s: shared-memory accumulators of the hot goods [0, hot); g: global ones
 __device__ __forceinline__ void acc_add_fixed(unsigned long long* s, unsigned long long* g, int hot, int j, float x) {
     if (x > 0.0f) {
         unsigned long long v = (unsigned long long)__float2ll_rn(x * kFixScaleF);
-        if (j < hot) atomicAdd(&s[j], v);
+        if (j < hot) shared_add_u64(&s[j], v);
         else atomicAdd(&g[j], v);
     }
 }
 __device__ __forceinline__ void acc_add_f64(unsigned long long* s, unsigned long long* g, int hot, int j, double x) {
     if (x > 0.0) {
-        if (j < hot) atomicAdd((double*)&s[j], x);
+        if (j < hot) shared_add_f64(&s[j], x);
         else atomicAdd((double*)&g[j], x);
     }
 }
@@ -194,7 +195,7 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
         for (int o = G / 2; o > 0; o >>= 1) pmax_u = fmaxf(pmax_u, __shfl_xor_sync(0xffffffffu, pmax_u, o));
         if (need) yh = pmax_u > 0.0f ? pmax_u : 1.0f;
     }
-    float yl = 0.0f, lo = 0.0f, hi = INFINITY, Rlast = 0.0f;
+    float yl = 0.0f, lo = 0.0f, hi = INFINITY, Rlast = 0.0f, Fprev = INFINITY;
     bool done = !valid;
     int steps = 0;
     while (__any_sync(0xffffffffu, !done)) {
@@ -209,10 +210,13 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             Rlast = Rs;
             const float ws = wf / yh;                       // w / y
             const float F = Rs - ws;
-            if (fabsf(F) <= 4.8e-7f * (Rs + ws) || ++steps >= rc.cap) {
+            // stop at a tight residual, or once Newton no longer reduces it (the
+            // FP32 noise floor of the two sums has been reached)
+            if (fabsf(F) <= 2e-8f * (Rs + ws) || (steps >= 2 && fabsf(F) > 0.5f * Fprev) || ++steps >= rc.cap) {
                 done = true;
                 if (steps >= rc.cap && tl == 0 && valid) capped++;
             } else {
+                Fprev = fabsf(F);
                 if (F > 0.0f) hi = yh; else lo = yh;
                 const float step = -F / fmaf(tau, Q, ws / yh);
                 ff yn = ff_add_f(ff_make(yh, yl), step);
