@@ -245,6 +245,28 @@ pdhcg_status pdhcg_row_prox(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precis
 pdhcg_status pdhcg_kkt(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precision prec,
                        const void* x, const double* p, double* out);
 
+/* pdhcg_kkt_noalloc: the same residuals as pdhcg_kkt for the FP64 value type,
+ * for callers that cannot allocate device memory when they need them (code
+ * running inside an allocator or memory-pool callback, a process whose device
+ * memory is fully reserved by another framework, a real-time loop that forbids
+ * allocation after start-up).  The paper has no counterpart; it is a
+ * deployment variant of the Section 5 residual.
+ *   mk, x[nnz] (double), p[m] (double): DEVICE pointers only, caller order,
+ *   the caller's CSR (no preprocessing beyond the row scaling of Section 5);
+ *   out[4]: host or device; r_primal, r_dual, r_gap, max of the three.
+ *   stream: cudaStream_t as void* (0 = legacy default stream); synchronous.
+ * No call allocates: all scratch lives in one file-scope device array sized
+ * for at most 262144 goods (about 4 MiB, held by every device that loads the
+ * library until the process exits); larger m returns PDHCG_ERR_INVALID, as do
+ * host input pointers and out-of-range indices (checked in the kernel).  The
+ * first call made with a given device current looks the array's device address
+ * up (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The array is shared by every call: each call clears what must start at zero,
+ * and calls that overlap on the GPU (other streams or host threads) race, so
+ * callers must serialise them. */
+pdhcg_status pdhcg_kkt_noalloc(const pdhcg_market* mk, const double* x, const double* p, double* out,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,7 @@ _SIGS = {
     "pdhcg_row_prox": (ctypes.c_int, [c_void_p, _P(pdhcg_market), ctypes.c_int, c_void_p, c_void_p, c_double,
                                       c_void_p, c_void_p, c_void_p]),
     "pdhcg_kkt": (ctypes.c_int, [c_void_p, _P(pdhcg_market), ctypes.c_int, c_void_p, c_void_p, c_void_p]),
+    "pdhcg_kkt_noalloc": (ctypes.c_int, [_P(pdhcg_market), c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -186,3 +187,8 @@ def pdhcg_row_prox(h, mk, prec, x_in, p, tau, x_new, s_out, c_out) -> int:
 
 def pdhcg_kkt(h, mk, prec, x, p, out) -> int:
     return _fn("pdhcg_kkt")(c_void_p(h), ctypes.byref(mk), prec, c_void_p(x), c_void_p(p), c_void_p(out))
+
+
+def pdhcg_kkt_noalloc(mk, x, p, out, stream=0) -> int:
+    """KKT residuals without any allocation (device inputs only); see pdhcg.h."""
+    return _fn("pdhcg_kkt_noalloc")(ctypes.byref(mk), c_void_p(x), c_void_p(p), c_void_p(out), c_void_p(stream))
