@@ -245,7 +245,7 @@ def main():
         dist.init_process_group("nccl")
     import __graft_entry__ as g
     g.build()
-    from paper_2506_06258_gb300 import api, capi, synth as S
+    from paper_2506_06258_gb300 import api, capi, shard, synth as S
 
     t_gen = time.perf_counter()
     mk = S.config3(n=cfg["n"], m=cfg["m"], nnz_target=cfg["nnz_target"], fp32=True)
@@ -283,11 +283,7 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ev0.elapsed_time(ev1), device=dev)
     iters = info.iters - info0.iters
     passes = info.passes - info0.passes
     value = world * iters / (ms * 1e-3)
