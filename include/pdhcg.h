@@ -115,6 +115,8 @@ typedef struct {
     int64_t prox_launches;     /* row-kernel launches that did a pass (timing=1)    */
     double kkt_ms;             /* device time of the KKT evaluations (timing=1)     */
     int64_t kernel_launches;   /* library kernels launched by the iteration loop    */
+    int64_t row_solve_evals;   /* MIXED: evaluations of the row equation, summed over
+                                  rows and passes (0 for FP64 and batched solves)   */
 } pdhcg_info;
 
 typedef struct pdhcg_handle_s* pdhcg_handle;

@@ -39,7 +39,7 @@ class pdhcg_info(ctypes.Structure):
                 ("r_primal", c_double), ("r_dual", c_double), ("r_gap", c_double), ("solve_ms", c_double),
                 ("setup_ms", c_double), ("bytes_moved", c_double), ("row_solve_capped", c_int32),
                 ("status", ctypes.c_int), ("prox_ms", c_double), ("prox_launches", c_int64), ("kkt_ms", c_double),
-                ("kernel_launches", c_int64)]
+                ("kernel_launches", c_int64), ("row_solve_evals", c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

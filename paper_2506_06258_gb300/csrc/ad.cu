@@ -89,7 +89,7 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
     CK(ensure(h->ad_p, m * sizeof(double)));
     CK(ensure(h->p0i, m * sizeof(double)));
     const double sum_w0 = device_sum((const double*)h->w.p, n, h->part2, s);
-    long long iters = 0, passes = 0, capped = 0;
+    long long iters = 0, passes = 0, capped = 0, evals = 0;
     int restarts = 0, outer = 0;
     double solve_ms = 0.0, setup_ms = 0.0;
     SolveResult r;
@@ -101,6 +101,7 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
         passes += r.passes;
         restarts += r.restarts;
         capped += r.capped;
+        evals += r.evals;
         solve_ms += r.solve_ms;
         setup_ms += r.setup_ms;
         // prices in caller order, then w_new = E p
@@ -156,6 +157,7 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
         r.passes = passes;
         r.restarts = restarts;
         r.capped = capped;
+        r.evals = evals;
         r.solve_ms = solve_ms;
         r.setup_ms = setup_ms;
         fill_info(info, r, P, out);

@@ -180,7 +180,7 @@ __global__ void batch_prep_kernel(BatchArgs a) {
         double rmx = 0.0;
         for (long long q = q0 + lane; q < q1; q += 32)
             rmx = fmax(rmx, a.val_f32 ? (double)((const float*)a.val)[q] : ((const double*)a.val)[q]);
-        rmx = warp_max_d(rmx);
+        rmx = row_scale<V>(warp_max_d(rmx));
         if (lane == 0) a.rowmax[i] = rmx;
         for (long long q = q0 + lane; q < q1; q += 32) {
             const double u = a.val_f32 ? (double)((const float*)a.val)[q] : ((const double*)a.val)[q];
@@ -213,16 +213,18 @@ __device__ void kkt_market(const BatchArgs& a, long long r0, long long r1, long 
     double mxx = 0.0, mg = 0.0, mxg = 0.0, my = 0.0;
     for (long long i = r0 + wid; i < r1; i += nw) {
         const long long q0 = a.rp[i], q1 = a.rp[i + 1];
-        double t = 0.0;
+        double t = 0.0, um = 0.0;
         for (long long q = q0 + lane; q < q1; q += 32) {
             double u = MIXED ? (double)((const float*)a.uv)[q] : ((const double*)a.uv)[q];
             double x = MIXED ? (double)((const float*)Xv)[q] : ((const double*)Xv)[q];
             t = fma(u, x, t);
+            um = fmax(um, u);
         }
         t = warp_sum_d(t);
+        um = warp_max_d(um);
         const double y = a.w[i] / t;
         if (lane == 0) tout[i] = t;
-        my = fmax(my, y);
+        my = fmax(my, y * um);         // y of the max-scaled row
         for (long long q = q0 + lane; q < q1; q += 32) {
             const int j = a.col[q];
             double u = MIXED ? (double)((const float*)a.uv)[q] : ((const double*)a.uv)[q];
@@ -289,13 +291,14 @@ __device__ void row_phase(const BatchArgs& a, const DevMarket& dm, long long r0,
     const long long units = (rows + rpw - 1) / rpw;
     float dxf = 0.0f;
     double dxd = 0.0;
+    int evals = 0;
     for (long long u = wid; u < units; u += nw) {
         const long long slot = u * rpw + lane / G;
         const bool valid = slot < rows;
         const int row = valid ? (int)(r0 + slot) : (int)r0;
         if (MIXED)
             row_mixed<G, LONG>(dm, (const float*)a.uv, (const float*)Xin, (float*)Xout, (float*)a.Xb, pff, acc, acc,
-                               a.tc, rc, row, valid, dxf, capped);
+                               a.tc, rc, row, valid, dxf, capped, evals);
         else
             row_fp64<G, LONG>(dm, (const double*)a.uv, (const double*)Xin, (double*)Xout, (double*)a.Xb, pcs, acc,
                               acc, a.tc, rc, row, valid, dxd, capped);
@@ -414,6 +417,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_solve_kernel(BatchArgs a) {
                 rc.fold_wd = S.fold_wgt;
                 rc.fold_w = (float)rc.fold_wd;
                 rc.cap = a.row_cap;
+                rc.seed = mix32((unsigned)S.passes * 2u + 1u);
                 const void* Xin = S.cur ? (const void*)X1 : (const void*)X0;
                 void* Xout = S.cur ? (void*)X0 : (void*)X1;
                 double dx2 = 0.0;

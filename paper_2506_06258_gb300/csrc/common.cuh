@@ -52,6 +52,7 @@ struct Ctl {
     long long chunk_acc;   // accepted iterations in the current chunk
     long long chunk_quota; // accepted iterations wanted per chunk
     long long capped;      // rows whose solve hit the round cap
+    long long evals;       // row-equation evaluations (MIXED row solves)
     unsigned int ticket;   // last-block-done counter of the dual kernel
     unsigned int ticket2;  // last-block-done counter of the KKT goods kernel
     int row_cap;           // active-set rounds per row solve
@@ -146,6 +147,40 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
     return quick_two_sum(y, __fdiv_rn(e.hi, __fmul_rn(2.0f, y)));
 }
 __device__ __forceinline__ bool ff_pos(ff a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
+// ---------------------------------------------------------------------------
+// stochastic rounding of FP32 iterates
+// ---------------------------------------------------------------------------
+// Near convergence a PDHCG increment tau (u_ij y_i - p_j) can fall below half
+// an ulp of a large x_ij; round-to-nearest then drops it every iteration and
+// the iteration stalls short of the tolerance.  Rounding to one of the two
+// neighbouring floats with probability proportional to proximity keeps every
+// stored value unbiased, so small increments accumulate in expectation.  The
+// random bits come from a counter-based mixer of (entry, pass), so runs are
+// deterministic.
+__device__ __forceinline__ unsigned mix32(unsigned x) {   // multiply-xorshift mixer
+    x ^= x >> 16;
+    x *= 0x9E3779B1u;                                      // 32-bit golden-ratio constant
+    x ^= x >> 15;
+    x *= 0x85EBCA77u;
+    x ^= x >> 13;
+    return x;
+}
+__device__ __forceinline__ unsigned sr_bits(long long idx, unsigned seed) {
+    return mix32((unsigned)idx ^ mix32((unsigned)(idx >> 32) + seed));
+}
+// a + b rounded stochastically with 16 random bits r
+__device__ __forceinline__ float sr_add(float a, float b, unsigned r) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));   // a + b = s + e
+    if (e == 0.0f || s == 0.0f) return s;
+    const int sb = __float_as_int(s);
+    const float nb = __int_as_float(((e > 0.0f) == (s > 0.0f)) ? sb + 1 : sb - 1);   // neighbour towards e
+    return (float)(r & 0xffffu) * (1.0f / 65536.0f) * fabsf(nb - s) < fabsf(e) ? nb : s;
+}
+
+// a > b for normalised float-float values
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
 // ---------------------------------------------------------------------------
 // shared-memory atomics with the state space spelled out (a generic-address
@@ -222,6 +257,19 @@ __device__ __forceinline__ double warp_max_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Row scale of the Section 5 preprocessing.  FP64 divides a row by its
+// maximum.  FP32 divides by the largest power of two not above the maximum, so
+// that FP32 utilities are scaled exactly (the scaled maximum lies in [1, 2));
+// the KKT evaluation multiplies y by the scaled row maximum to report the
+// residuals of the max-scaled market.
+template <typename V>
+__device__ __forceinline__ double row_scale(double mx) {
+    if (sizeof(V) == sizeof(double)) return mx;
+    int e;
+    frexp(mx, &e);              // mx = f 2^e, f in [0.5, 1)
+    return ldexp(1.0, e - 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,16 +28,18 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_kernel(DevMarket mk, const 
     double mx = 0.0, mg = 0.0, mxg = 0.0, my = 0.0;
     for (long long i = gw; i < mk.n; i += nw) {
         const long long b = mk.rp[i], e = mk.rp[i + 1];
-        double t = 0.0;
+        double t = 0.0, um = 0.0;
         for (long long q = b + lane; q < e; q += 32) {
             double u = MIXED ? (double)((const float*)mk.uv)[q] : ((const double*)mk.uv)[q];
             double x = MIXED ? (double)((const float*)Xv)[q] : ((const double*)Xv)[q];
             t = fma(u, x, t);
+            um = fmax(um, u);
         }
         t = warp_sum_d(t);
+        um = warp_max_d(um);
         const double y = mk.w[i] / t;
         if (lane == 0 && kb.t_out) kb.t_out[i] = t;
-        my = fmax(my, y);
+        my = fmax(my, y * um);         // y of the max-scaled row
         for (long long q = b + lane; q < e; q += 32) {
             const int j = mk.cj[q];
             double u = MIXED ? (double)((const float*)mk.uv)[q] : ((const double*)mk.uv)[q];
@@ -116,11 +118,17 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_mixed_kernel(DevMarket mk, 
     for (long long i = gw; i < mk.n; i += nw) {
         const long long b = mk.rp[i], e = mk.rp[i + 1];
         ff t = ff_make(0.0f, 0.0f);
-        for (long long q = b + lane; q < e; q += 32) t = ff_add(t, two_prod(U[q], Xv[q]));
+        float um = 0.0f;
+        for (long long q = b + lane; q < e; q += 32) {
+            const float u = U[q];
+            t = ff_add(t, two_prod(u, Xv[q]));
+            um = fmaxf(um, u);
+        }
         t = group_sum<32>(t);
+        for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
         const ff y = ff_div(ff_from_double(mk.w[i]), t);
         if (lane == 0 && kb.t_out) kb.t_out[i] = ff_to_double(t);
-        my = fmax(my, ff_to_double(y));
+        my = fmax(my, ff_to_double(y) * (double)um);   // y of the max-scaled row
         for (long long q = b + lane; q < e; q += 32) {
             const int j = mk.cj[q];
             const float u = U[q], x = Xv[q];

@@ -44,7 +44,7 @@ __global__ void col_degree_kernel(long long nnz, const int* __restrict__ col, in
     }
 }
 
-// row maximum, scaled utilities, relabelled goods, initial x
+// row scale (row_scale), scaled utilities, relabelled goods, initial x
 template <typename V>
 __global__ void scale_kernel(int n, const long long* __restrict__ rp, const int* __restrict__ col, const void* val,
                              int val_f32, const int* __restrict__ rank, const int* __restrict__ deg,
@@ -60,7 +60,7 @@ __global__ void scale_kernel(int n, const long long* __restrict__ rp, const int*
             const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
             mx = fmax(mx, u);
         }
-        mx = warp_max_d(mx);
+        mx = row_scale<V>(warp_max_d(mx));
         if (lane == 0) rowmax[i] = mx;
         for (long long q = b + lane; q < e; q += 32) {
             const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
@@ -140,6 +140,25 @@ void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, 
 void k_scatter_goods(int m, const int* rank, const double* src, double* dst_int, cudaStream_t s) {
     scatter_goods_kernel<<<grid_for(m), 256, 0, s>>>(m, rank, src, dst_int);
 }
+// FP32 rows are scaled by a power of two (row_scale); t of the max-scaled row
+// is t / max_j u_ij of the stored row.
+__global__ void max_scaled_t_kernel(int n, const long long* __restrict__ rp, const float* __restrict__ uv,
+                                    const double* __restrict__ t, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = gw; i < n; i += nw) {
+        float um = 0.0f;
+        for (long long q = rp[i] + lane; q < rp[i + 1]; q += 32) um = fmaxf(um, uv[q]);
+        for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+        if (lane == 0) out[i] = t[i] / (double)um;
+    }
+}
+
+void k_max_scaled_t(int n, const long long* rp, const float* uv, const double* t, double* out, cudaStream_t s) {
+    max_scaled_t_kernel<<<grid_for((long long)n * 32), 256, 0, s>>>(n, rp, uv, t, out);
+}
+
 void k_util_out(int n, const double* t, const double* rowmax, double* out, cudaStream_t s) {
     util_out_kernel<<<grid_for(n), 256, 0, s>>>(n, t, rowmax, out);
 }

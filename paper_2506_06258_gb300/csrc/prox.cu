@@ -29,7 +29,7 @@ namespace pdhcg {
 template <int G>
 __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned long long* counter, const void* Xin,
                              void* Xout, const IterBufs& bf, const float2* sp, unsigned long long* acc_s,
-                             const RowCtx& rc, float& dxf, int& capped) {
+                             const RowCtx& rc, float& dxf, int& capped, int& evals) {
     constexpr int rpw = 32 / G;
     const int lane = threadIdx.x & 31;
     const long long units = (bk.count + rpw - 1) / rpw;
@@ -57,7 +57,7 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
                 row_load<G>(mk, U, Xi, rn, vn, nx);
             }
             row_mixed_core<G, false>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
-                                     rc_row, vc, dxf, capped, cr);
+                                     rc_row, vc, dxf, capped, evals, cr);
         }
     }
 }
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     rc.fold_wd = ctl->fold_wgt;
     rc.fold_w = (float)rc.fold_wd;
     rc.cap = ctl->row_cap;
+    rc.seed = mix32((unsigned)ctl->passes * 2u + 1u);
     const int cur = ctl->cur;
     const void* Xin = fixed ? Xin_fixed : (cur ? bf.X[1] : bf.X[0]);
     void* Xout = fixed ? Xout_fixed : (cur ? bf.X[0] : bf.X[1]);
@@ -89,17 +90,17 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     const int lane = threadIdx.x & 31;
     float dxf = 0.0f;
     double dxd = 0.0;
-    int capped = 0;
+    int capped = 0, evals = 0;
 
     for (int bi = 0; bi < mk.nb; bi++) {
         const Bucket bk = mk.buckets[bi];
         const int g = bk.g;
         if (MIXED && !bk.chunks) {
             switch (g) {
-                case 4: bucket_mixed<4>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
-                case 8: bucket_mixed<8>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
-                case 16: bucket_mixed<16>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
-                default: bucket_mixed<32>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped); break;
+                case 4: bucket_mixed<4>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                case 8: bucket_mixed<8>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                case 16: bucket_mixed<16>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                default: bucket_mixed<32>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
             }
             continue;
         }
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
                     R.e = valid ? mk.rp[row + 1] : 0;
                     row_mixed_core<32, true>(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout,
                                              (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf,
-                                             capped, R);
+                                             capped, evals, R);
                 } else {
                     const double* U = (const double*)mk.uv;
                     double* Xo = (double*)Xout;
@@ -142,17 +143,19 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     double v = MIXED ? (double)dxf : dxd;
     v = warp_sum_d(v);
     __shared__ double red[kWarps];
-    __shared__ int capred;
-    if (threadIdx.x == 0) capred = 0;
+    __shared__ int capred, evred;
+    if (threadIdx.x == 0) capred = evred = 0;
     __syncthreads();
     if (lane == 0) red[threadIdx.x >> 5] = v;
     if (capped) atomicAdd(&capred, capped);
+    if (evals) atomicAdd(&evred, evals);
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < kWarps; w++) t += red[w];
         bf.part[blockIdx.x] = t;
         if (capred) atomicAdd((unsigned long long*)&ctl->capped, (unsigned long long)capred);
+        if (evred) atomicAdd((unsigned long long*)&ctl->evals, (unsigned long long)evred);
     }
     for (int j = threadIdx.x; j < mk.hot; j += blockDim.x) {
         unsigned long long a = acc_s[j];
@@ -287,9 +290,15 @@ __global__ void flush_x_kernel(long long nnz, IterBufs bf, Ctl* ctl) {
     V* xb = (V*)bf.Xb;
     const double wgt = ctl->fold_wgt;
     const V wv = (V)wgt;
+    const unsigned seed = mix32((unsigned)ctl->passes * 2u + 2u);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz; i += (long long)gridDim.x * blockDim.x) {
         V xv = x[i];
-        xb[i] = (wgt == 1.0) ? xv : xb[i] + wv * (xv - xb[i]);
+        if (wgt == 1.0) {
+            xb[i] = xv;
+        } else {
+            if constexpr (sizeof(V) == sizeof(float)) xb[i] = sr_add(xb[i], wv * (xv - xb[i]), sr_bits(i, seed) >> 16);
+            else xb[i] = xb[i] + wv * (xv - xb[i]);
+        }
     }
 }
 __global__ void flush_p_kernel(int m, IterBufs bf, Ctl* ctl) {
@@ -415,6 +424,7 @@ __global__ void ctl_fixed_kernel(Ctl* ctl, double tau, int cap) {
     ctl->cur = 0;
     ctl->row_cap = cap;
     ctl->capped = 0;
+    ctl->evals = 0;
 }
 
 void launch_to_ff(int m, const double* p, float2* pff, cudaStream_t s) {

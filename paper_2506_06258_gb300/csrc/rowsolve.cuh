@@ -59,6 +59,7 @@ struct RowCtx {
     double fold_wd;
     bool fold;
     int cap;
+    unsigned seed;      // pass counter mixed into the stochastic-rounding bits
 };
 
 // ---------------------------------------------------------------------------
@@ -74,10 +75,24 @@ struct RowCtx {
 // the support near equilibrium, and tau p_j can dwarf x_j), so p is carried in
 // float-float, y = y_h + y_l likewise, and
 //     d_j = fma(-u, y_l, fma(-u, y_h, p_h) + p_l)
-// is exact up to rounding relative to d_j itself; everything else is FP32.
-// Newton steps from y_0 = w / (u^T x^k) (the paper's trial value), safeguarded
-// by a bracket [lo, hi] on the sign of F, stop when |F| is at the FP32 noise
-// level of its two terms.
+// is exact up to rounding relative to d_j itself.  The sum is split as
+//     sum_j u_j [x_j - tau d_j]_+ = s0 - C(y),  s0 = u^T x^k,
+//     C(y) = sum_j u_j min(tau d_j, x_j),
+// with s0 and w / y in float-float and only the correction C in FP32: its
+// rounding error scales with sum_j u_j |min(tau d_j, x_j)|, which shrinks with
+// the step x^{k+1} - x^k, so the root is resolved far below the FP32 noise of
+// sum u x itself.
+// Iteration: with the active set of y_k frozen, C is affine in y
+// (slope -tau Q, Q = sum_active u^2), and the frozen equation
+//     F_k + tau Q delta + w delta / (y_k (y_k + delta)) = 0
+// is a quadratic in delta whose root is taken in cancellation-free form.
+// min(tau d_j, x_j) is concave in y, so the frozen model lies below F and its
+// root is an upper bound of y*: after the first step the iterates decrease
+// monotonically to y* and stop once the active set no longer changes (the
+// same finite active-set iteration as the FP64 form, written in y).  Start
+// at y_0 = w / s0 (the paper's trial value); a bracket [lo, hi] on the sign of
+// F guards against rounding; stop when |F| is below the rounding bound of its
+// evaluation or y no longer moves.
 // ---------------------------------------------------------------------------
 // Entries of one row held by one lane (register-resident rows).
 struct RowRegs {
@@ -117,7 +132,7 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
                                float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
                                const float2* sp, unsigned long long* acc_s, unsigned long long* acc_g,
                                double* __restrict__ t_out, const RowCtx& rc, int row, bool valid, float& dx2,
-                               int& capped, RowRegs& R) {
+                               int& capped, int& evals, RowRegs& R) {
     const int tl = (threadIdx.x & 31) & (G - 1);
     const long long b = R.b;
     const long long e = R.e;
@@ -127,7 +142,7 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
     const int span = G * kSlots;
     const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
 
-    float rph[kSlots], rpl[kSlots], rxn[kSlots];
+    float rph[kSlots], rpl[kSlots], rtd[kSlots];
     float* ru = R.u;
     float* rx = R.x;
     int* rj = R.j;
@@ -158,30 +173,33 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             }
         }
     };
-    // residual terms at (yh, yl): R = sum u x_new, Q = sum_active u^2
-    auto eval_chunk = [&](float yh, float yl, float& Rs, float& Q) {
+    // at (yh, yl): C = sum u min(tau d, x), A = sum u |min(tau d, x)|,
+    // Q = sum_active u^2 (active: tau d < x), and tau d of every entry
+    auto eval_chunk = [&](float yh, float yl, float& C, float& A, float& Q) {
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
             const float u = ru[k];
             const float d = fmaf(-u, yl, fmaf(-u, yh, rph[k]) + rpl[k]);
-            float xn = fmaf(-tau, d, rx[k]);
-            xn = (rj[k] >= 0 && xn > 0.0f) ? xn : 0.0f;
-            rxn[k] = xn;
-            Rs = fmaf(u, xn, Rs);
-            if (xn > 0.0f) Q = fmaf(u, u, Q);
+            const float td = tau * d;
+            rtd[k] = td;
+            const float cr = fminf(td, rx[k]);
+            C = fmaf(u, cr, C);
+            A = fmaf(u, fabsf(cr), A);
+            if (td < rx[k]) Q = fmaf(u, u, Q);
         }
     };
 
-    // ---- starting point: y_0 = w / (u^T x^k) ----
-    float s0 = 0.0f;
+    // ---- s0 = u^T x^k in float-float; starting point y_0 = w / s0 ----
+    ff s0 = ff_make(0.0f, 0.0f);
     for (int c = 0; c < nch; c++) {
         if (LONG) load_chunk(c);
 #pragma unroll
-        for (int k = 0; k < kSlots; k++) s0 = fmaf(ru[k], rx[k], s0);
+        for (int k = 0; k < kSlots; k++) s0 = ff_add(s0, two_prod(ru[k], rx[k]));
     }
     if (!LONG) gather_p();
     s0 = group_sum<G>(s0);
-    float yh = (s0 > 0.0f) ? wf / s0 : 0.0f;
+    const ff wff = ff_from_double(wd);
+    float yh = (s0.hi > 0.0f) ? wf / s0.hi : 0.0f;
     const bool need = !(yh > 0.0f) || !isfinite(yh);
     if (__any_sync(0xffffffffu, need)) {
         // x^k = 0 on this row: at y = max_j p_j / u_j every entry has d <= 0
@@ -195,40 +213,52 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
         for (int o = G / 2; o > 0; o >>= 1) pmax_u = fmaxf(pmax_u, __shfl_xor_sync(0xffffffffu, pmax_u, o));
         if (need) yh = pmax_u > 0.0f ? pmax_u : 1.0f;
     }
-    float yl = 0.0f, lo = 0.0f, hi = INFINITY, Rlast = 0.0f, Fprev = INFINITY;
+    // rounding bound of C: a lane adds nch*kSlots terms, then log2(G) levels
+    const float cnoise = 1.2e-7f * (sqrtf((float)(nch * kSlots)) + 3.0f);
+    float yl = 0.0f, Clast = 0.0f;
+    ff lo = ff_make(0.0f, 0.0f), hi = ff_make(INFINITY, 0.0f);   // bracket, in float-float
     bool done = !valid;
-    int steps = 0;
+    int steps = 0, nev = 0;
     while (__any_sync(0xffffffffu, !done)) {
-        float Rs = 0.0f, Q = 0.0f;
+        float C = 0.0f, A = 0.0f, Q = 0.0f;
         for (int c = 0; c < nch; c++) {
             if (LONG) { load_chunk(c); gather_p(); }
-            eval_chunk(yh, yl, Rs, Q);
+            eval_chunk(yh, yl, C, A, Q);
         }
-        Rs = group_sum<G>(Rs);
+        C = group_sum<G>(C);
+        A = group_sum<G>(A);
         Q = group_sum<G>(Q);
         if (!done) {
-            Rlast = Rs;
-            const float ws = wf / yh;                       // w / y
-            const float F = Rs - ws;
-            // stop at a tight residual, or once Newton no longer reduces it (the
-            // FP32 noise floor of the two sums has been reached)
-            if (fabsf(F) <= 2e-8f * (Rs + ws) || (steps >= 2 && fabsf(F) > 0.5f * Fprev) || ++steps >= rc.cap) {
+            nev++;
+            Clast = C;
+            const ff ws = ff_div(wff, ff_make(yh, yl));    // w / y
+            const ff D = ff_sub(s0, ws);
+            const float F = (D.hi - C) + D.lo;
+            // rounding bound of F: C's FP32 sum, plus the float-float
+            // resolution of p and y seen through tau sum u p ~ tau Q y
+            const float aQ = tau * Q;
+            const float floor = fmaf(cnoise, A, fmaf(3e-14f, aQ * yh, 2e-8f * ws.hi));
+            if (fabsf(F) <= floor || ++steps >= rc.cap) {
                 done = true;
                 if (steps >= rc.cap && tl == 0 && valid) capped++;
             } else {
-                Fprev = fabsf(F);
-                if (F > 0.0f) hi = yh; else lo = yh;
-                const float step = -F / fmaf(tau, Q, ws / yh);
-                ff yn = ff_add_f(ff_make(yh, yl), step);
-                if (!(yn.hi > lo && yn.hi < hi)) {          // Newton left the bracket
-                    const float mid = isinf(hi) ? 2.0f * yh : (lo > 0.0f ? 0.5f * (lo + hi) : 0.5f * hi);
-                    yn = ff_make(mid, 0.0f);
-                }
+                if (F > 0.0f) hi = ff_make(yh, yl); else lo = ff_make(yh, yl);
+                // root of the frozen-active-set quadratic a d^2 + b d + c = 0,
+                // b = sum u x_new + tau Q y >= 0
+                const float bq = fmaf(aQ, yh, F + ws.hi);
+                const float cq = F * yh;
+                const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
+                const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
+                ff yn = ff_add_f(ff_make(yh, yl), delta);
+                if (!(ff_gt(yn, lo) && ff_gt(hi, yn)))       // rounding left the bracket
+                    yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
+                if (yn.hi == yh && yn.lo == yl) done = true;   // no representable progress
                 yh = yn.hi;
                 yl = yn.lo;
             }
         }
     }
+    if (valid && tl == 0) evals += nev;
 
     // ---- new iterate (last evaluation), average fold, column sums ----
     const float fw = rc.fold_w;
@@ -236,22 +266,27 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
         if (LONG) {
             load_chunk(c);
             gather_p();
-            float Rs = 0.0f, Q = 0.0f;
-            eval_chunk(yh, yl, Rs, Q);
+            float C = 0.0f, A = 0.0f, Q = 0.0f;
+            eval_chunk(yh, yl, C, A, Q);
         }
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
             if (rj[k] < 0) continue;
             const long long idx = b + (long long)c * span + k * G + tl;
-            const float xn = rxn[k];
+            const unsigned rb = sr_bits(idx, rc.seed);
+            // x^{k+1} = [x^k - tau d]_+, stochastically rounded
+            const float xn = rtd[k] < rx[k] ? sr_add(rx[k], -rtd[k], rb) : 0.0f;
             __stcs(Xout + idx, xn);
             const float d = xn - rx[k];
             dx2 = fmaf(d, d, dx2);
-            if (rc.fold) Xb[idx] = (fw == 1.0f) ? rx[k] : fmaf(fw, rx[k] - Xb[idx], Xb[idx]);
+            if (rc.fold) {
+                const float xb = Xb[idx];
+                Xb[idx] = (fw == 1.0f) ? rx[k] : sr_add(xb, fw * (rx[k] - xb), rb >> 16);
+            }
             acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
         }
     }
-    if (valid && tl == 0) t_out[row] = (double)Rlast;
+    if (valid && tl == 0) t_out[row] = ((double)s0.hi + (double)s0.lo) - (double)Clast;
 }
 
 // Convenience form (loads the row itself): used by the batched kernel.
@@ -259,7 +294,7 @@ template <int G, bool LONG>
 __device__ void row_mixed(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
                           float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
                           unsigned long long* acc_s, unsigned long long* acc_g, double* __restrict__ t_out,
-                          const RowCtx& rc, int row, bool valid, float& dx2, int& capped) {
+                          const RowCtx& rc, int row, bool valid, float& dx2, int& capped, int& evals) {
     RowRegs R;
     if (LONG) {
         R.b = valid ? mk.rp[row] : 0;
@@ -267,7 +302,7 @@ __device__ void row_mixed(const DevMarket& mk, const float* __restrict__ U, cons
     } else {
         row_load<G>(mk, U, Xin, row, valid, R);
     }
-    row_mixed_core<G, LONG>(mk, U, Xin, Xout, Xb, pff, pff, acc_s, acc_g, t_out, rc, row, valid, dx2, capped, R);
+    row_mixed_core<G, LONG>(mk, U, Xin, Xout, Xb, pff, pff, acc_s, acc_g, t_out, rc, row, valid, dx2, capped, evals, R);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,7 +332,7 @@ __device__ void row_fp64(const DevMarket& mk, const double* __restrict__ U, cons
                 int j = __ldg(mk.cj + idx);
                 double u = __ldg(U + idx);
                 double x = Xin[idx];
-                rj[k] = j; ru[k] = u; rx[k] = x; ra[k] = x - rc.tau * __ldg(pc + j);
+                rj[k] = j; ru[k] = u; rx[k] = x; ra[k] = x - rc.tau * pc[j];   // pc may live in shared memory
             } else {
                 rj[k] = 0; ru[k] = 0.0; rx[k] = 0.0; ra[k] = 0.0;
             }

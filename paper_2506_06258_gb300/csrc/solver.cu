@@ -519,8 +519,9 @@ pdhcg_status session_step(pdhcg_handle h, long long chunks) {
         S.best = S.use_avg ? kavg : kcur;
         const double kc = S.best.kkt;
         if (prm.verbose)
-            fprintf(stderr, "[pdhcg] it %lld passes %lld kkt cur %.3e avg %.3e eta %.3e omega %.3e restarts %d\n",
-                    c.iters, c.passes, kcur.kkt, kavg.kkt, c.eta, c.omega, S.restarts);
+            fprintf(stderr, "[pdhcg] it %lld passes %lld kkt cur %.3e (p %.2e d %.2e g %.2e) avg %.3e eta %.3e omega %.3e "
+                    "restarts %d\n", c.iters, c.passes, kcur.kkt, kcur.r_primal, kcur.r_dual, kcur.r_gap, kavg.kkt, c.eta,
+                    c.omega, S.restarts);
         if (kc <= prm.tol) { S.converged = true; S.status = PDHCG_OK; break; }
         if (c.iters >= prm.max_iter || c.passes >= 4 * prm.max_iter + 10000) {
             S.status = PDHCG_ERR_NOT_CONVERGED;
@@ -592,6 +593,7 @@ void session_result(pdhcg_handle h, SolveResult* res) {
     res->passes = c.passes;
     res->restarts = S.restarts;
     res->capped = c.capped;
+    res->evals = c.evals;
     res->solve_ms = S.t_loop;
     res->setup_ms = S.t_setup;
     res->converged = S.converged;
@@ -746,6 +748,7 @@ void fill_info(pdhcg_info* info, const SolveResult& r, const Prepared& P, pdhcg_
     info->prox_launches = r.prox_launches;
     info->kkt_ms = r.kkt_ms;
     info->kernel_launches = r.launches;
+    info->row_solve_evals = r.evals;
 }
 
 pdhcg_status pdhcg_fisher_begin(pdhcg_handle h, const pdhcg_market* mk, const pdhcg_params* prm,
@@ -852,7 +855,10 @@ pdhcg_status pdhcg_row_prox(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precis
     launch_prox_fixed(mixed, P.dm, xi, xo, (const double*)h->p0i.p, tau, (unsigned long long*)h->acc.p,
                       (double*)h->t.p, (double*)h->c_cur.p, (double*)h->part.p, (Ctl*)h->ctl.p, s);
     CK(cudaGetLastError());
-    if (so) CK(cudaMemcpyAsync(so, h->t.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (so) {
+        if (mixed) k_max_scaled_t(P.n, (const long long*)P.dm.rp, (const float*)P.dm.uv, (const double*)h->t.p, so, s);
+        else CK(cudaMemcpyAsync(so, h->t.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     if (co) k_gather_goods(P.m, (const int*)h->rank.p, (const double*)h->c_cur.p, co, s);
     CK(copy_out(x_new, xo, P.nnz * vb, s));
     CK(copy_out(s_out, so, P.n * sizeof(double), s));

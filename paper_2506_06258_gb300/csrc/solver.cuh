@@ -55,7 +55,7 @@ struct SolveResult {
     double* p = nullptr;
     double* t = nullptr;
     KktOut kkt = {};
-    long long iters = 0, passes = 0, capped = 0;
+    long long iters = 0, passes = 0, capped = 0, evals = 0;
     int restarts = 0;
     double solve_ms = 0.0, setup_ms = 0.0;
     double prox_ms = 0.0, kkt_ms = 0.0;

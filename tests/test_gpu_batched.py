@@ -27,7 +27,10 @@ def _small_batch(B, seed, fp32):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_batch_matches_oracle(solver, prec):
     bt = _small_batch(12, 77, fp32=(prec == "mixed"))
-    tol = 1e-8 if prec == "fp64" else 1e-6
+    # MIXED is solved a little below 1e-6: at KKT 1e-6 the price error bound
+    # scales with 1 / (smallest price), and these small markets carry goods
+    # priced at a few percent of the mean
+    tol = 1e-8 if prec == "fp64" else 2e-7
     out = solver.solve_batched(bt, tol=tol, precision=prec)
     assert out.status == 0, [i["status"] for i in out.info]
     p = host(out.p)
