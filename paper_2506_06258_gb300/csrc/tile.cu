@@ -1,0 +1,556 @@
+// Row kernel of the MIXED form over CSR tiles: steps a2-a4 of one PDHCG pass
+// (the row subproblems of Section 2.2 with the column sums of Eq. update:py
+// and the running average of Alg. 2 fused).
+//
+// Buyers are cut, in CSR order, into tiles of whole rows holding at most
+// kTileCap entries and kTileRows rows.  A persistent block takes every
+// gridDim.x-th tile.  A tile's utilities, x^k, x-bar and good ids, with its
+// row offsets and budgets, arrive by bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier) in one of two shared-memory
+// stages, so the next tile streams in while the current one is solved.  Each
+// thread owns kTileE consecutive entries of the tile.  Row sums are per-thread
+// runs combined by a segmented warp scan and shared-memory atomics, and the
+// row equations of all rows of the tile are iterated together: one evaluation
+// is one sweep over the tile's entries followed by one update per row, until
+// every row has converged.  The arithmetic is that of row_mixed_core: s0 and
+// w/y in float-float, FP32 corrections C = sum u min(tau d, x), the
+// frozen-active-set quadratic step, stochastic rounding of x^{k+1} and x-bar.
+// Rows longer than a tile go to the warp-chunked path after the tiles.
+#include <cstdlib>
+
+#include "common.cuh"
+#include "rowsolve.cuh"
+
+namespace pdhcg {
+
+namespace {
+
+// ---- shared-memory stage layout (bytes) ----
+constexpr int kTileRowBuf = kTileRows + 4;                  // staged row_ptr / w entries
+constexpr int kOffU = 0;
+constexpr int kOffX = kOffU + kTileCap * 4;
+constexpr int kOffXb = kOffX + kTileCap * 4;
+constexpr int kOffJ = kOffXb + kTileCap * 4;
+constexpr int kOffRp = kOffJ + kTileCap * 4;
+constexpr int kOffW = kOffRp + kTileRowBuf * 8;
+constexpr int kStageBytes = kOffW + kTileRowBuf * 8;
+static_assert(kStageBytes % 16 == 0, "stage size must keep 16-byte alignment");
+static_assert(kTileCap == kThreads * kTileE, "tile capacity");
+
+struct TileHdr {
+    long long ea, eb, A;   // entries [ea, eb); stage holds entries from A = ea rounded down to 4
+    int ra, rb;            // rows [ra, rb)
+};
+
+// per-row state of the tile being solved
+struct TileRows {
+    double s0[kTileRows];
+    float yh[kTileRows], yl[kTileRows];
+    float loh[kTileRows], lol[kTileRows], hih[kTileRows], hil[kTileRows];
+    float C[kTileRows], A[kTileRows], Q[kTileRows], Clast[kTileRows];
+    int pmax[kTileRows];            // max_j p_j / u_j as float bits (start of an empty row)
+    int steps[kTileRows], nev[kTileRows], done[kTileRows];
+    int off[kTileRows + 1];         // entry offsets of the rows, relative to A
+};
+
+// ---- bulk copies and mbarriers ----
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state) : "r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("" ::"l"(state));
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait: false after ~2^24 polls (seconds), never spins forever
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 24); it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void proxy_fence() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void shared_add_f32(float* p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void shared_max_s32(int* p, int v) {
+    asm volatile("red.shared.max.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+// thread 0: start the copies of tile t into a stage
+__device__ void tile_issue(const DevMarket& mk, const float* Xin, const float* Xb, bool fold, int t,
+                           unsigned char* st, unsigned long long* bar, TileHdr* hd) {
+    const int2 rr = mk.tile_rows[t];
+    const longlong2 ee = mk.tile_ent[t];
+    const long long A = ee.x & ~3LL;
+    const unsigned vb = (unsigned)(((ee.y - A) + 3) & ~3LL) * 4u;        // <= kTileCap * 4
+    const int ra2 = rr.x & ~1;
+    const unsigned nrp = (unsigned)((rr.y + 1 - ra2 + 1) & ~1);          // rp[ra2, ra2 + nrp)
+    const unsigned nw = (unsigned)((rr.y - ra2 + 1) & ~1);               // w[ra2, ra2 + nw)
+    hd->ea = ee.x;
+    hd->eb = ee.y;
+    hd->A = A;
+    hd->ra = rr.x;
+    hd->rb = rr.y;
+    const unsigned bytes = vb * (fold ? 4u : 3u) + (nrp + nw) * 8u;
+    proxy_fence();
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(st + kOffU, (const float*)mk.uv + A, vb, bar);
+    bulk_g2s(st + kOffX, Xin + A, vb, bar);
+    if (fold) bulk_g2s(st + kOffXb, Xb + A, vb, bar);
+    bulk_g2s(st + kOffJ, mk.cj + A, vb, bar);
+    bulk_g2s(st + kOffRp, mk.rp + ra2, nrp * 8u, bar);
+    bulk_g2s(st + kOffW, mk.w + ra2, nw * 8u, bar);
+}
+
+// Segmented suffix sums over the lanes of a warp: lanes with equal keys form
+// contiguous runs (keys are row ids in entry order); afterwards the first lane
+// of each run holds the run's total.  Returns true on that lane.
+__device__ __forceinline__ bool seg_head(int key) {
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    return lane == 0 || prev != key;
+}
+__device__ __forceinline__ void seg_sum3(int key, float& a, float& b, float& c) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int k2 = __shfl_down_sync(0xffffffffu, key, o);
+        const float a2 = __shfl_down_sync(0xffffffffu, a, o);
+        const float b2 = __shfl_down_sync(0xffffffffu, b, o);
+        const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+        if (lane + o < 32 && k2 == key) { a += a2; b += b2; c += c2; }
+    }
+}
+__device__ __forceinline__ void seg_sum_ff(int key, ff& v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int k2 = __shfl_down_sync(0xffffffffu, key, o);
+        const ff v2 = ff_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+        if (lane + o < 32 && k2 == key) v = ff_add(v, v2);
+    }
+}
+
+}  // namespace
+
+size_t tile_smem_bytes(int hot) { return (size_t)hot * 16 + 2 * (size_t)kStageBytes; }
+
+__global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const void* Xin_fixed, void* Xout_fixed,
+                                                         IterBufs bf, Ctl* ctl, int fixed) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TileRows R;
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ TileHdr hdr[2];
+    if (!ctl->active) return;
+    const int tid = threadIdx.x;
+    RowCtx rc;
+    rc.tau = ctl->tau;
+    rc.tau_hi = (float)rc.tau;
+    rc.tau_lo = (float)(rc.tau - (double)rc.tau_hi);
+    rc.fold = !fixed && ctl->fold_pending;
+    rc.fold_wd = ctl->fold_wgt;
+    rc.fold_w = (float)rc.fold_wd;
+    rc.cap = ctl->row_cap;
+    rc.seed = mix32((unsigned)ctl->passes * 2u + 1u);
+    const int cur = ctl->cur;
+    const float* Xin = (const float*)(fixed ? Xin_fixed : (cur ? bf.X[1] : bf.X[0]));
+    float* Xout = (float*)(fixed ? Xout_fixed : (cur ? bf.X[0] : bf.X[1]));
+    float* Xb = (float*)bf.Xb;
+    const float tau = rc.tau_hi;
+    const float fw = rc.fold_w;
+    const int hot = mk.hot;
+
+    unsigned long long* acc_s = (unsigned long long*)smem;
+    float2* sp = (float2*)(acc_s + hot);
+    unsigned char* stages = smem + (size_t)hot * 16;
+    for (int j = tid; j < hot; j += kThreads) {
+        acc_s[j] = 0ull;
+        sp[j] = bf.pff[j];
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    float dxf = 0.0f;
+    int capped = 0, evals = 0;
+    unsigned par0 = 0u, par1 = 0u;      // mbarrier phase parity of the two stages
+    bool timed_out = false;
+    int s = 0;
+    int t = blockIdx.x;
+    if (tid == 0 && t < mk.ntiles) tile_issue(mk, Xin, Xb, rc.fold, t, stages, &bar[0], &hdr[0]);
+
+    for (; t < mk.ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < mk.ntiles)
+            tile_issue(mk, Xin, Xb, rc.fold, tn, stages + (size_t)(s ^ 1) * kStageBytes, &bar[s ^ 1], &hdr[s ^ 1]);
+        const bool ok = mbar_wait(&bar[s], s ? par1 : par0);
+        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        if (s) par1 ^= 1u; else par0 ^= 1u;
+
+        // ================= solve tile t from stage s =================
+        const unsigned char* st = stages + (size_t)s * kStageBytes;
+        const float* su = (const float*)(st + kOffU);
+        const float* sx = (const float*)(st + kOffX);
+        const float* sxb = (const float*)(st + kOffXb);
+        const int* sj = (const int*)(st + kOffJ);
+        const long long* srp = (const long long*)(st + kOffRp);
+        const double* sw = (const double*)(st + kOffW);
+        const TileHdr hd = hdr[s];
+        const int nr = hd.rb - hd.ra;
+        const long long A0 = hd.A;
+        const int ro = hd.ra & 1;
+        const int L0 = (int)(hd.ea - A0), L1 = (int)(hd.eb - A0);
+
+        if (tid <= nr) R.off[tid] = (int)(srp[ro + tid] - A0);
+        if (tid < nr) {
+            R.s0[tid] = 0.0;
+            R.pmax[tid] = 0;
+            R.steps[tid] = 0;
+            R.nev[tid] = 0;
+            R.done[tid] = 0;
+            R.loh[tid] = 0.0f;
+            R.lol[tid] = 0.0f;
+            R.hih[tid] = INFINITY;
+            R.hil[tid] = 0.0f;
+        }
+        __syncthreads();
+
+        // ---- own entries: local positions Lb .. Lb + kTileE - 1 ----
+        const int Lb = tid * kTileE;
+        float u[kTileE], x[kTileE], ph[kTileE], pl[kTileE], td[kTileE];
+        int lr[kTileE], jj[kTileE];
+        {
+            const float4* u4 = (const float4*)(su + Lb);
+            const float4* x4 = (const float4*)(sx + Lb);
+            const int4* j4 = (const int4*)(sj + Lb);
+#pragma unroll
+            for (int q = 0; q < kTileE / 4; q++) {
+                const float4 a = u4[q], c = x4[q];
+                const int4 g = j4[q];
+                u[4 * q] = a.x; u[4 * q + 1] = a.y; u[4 * q + 2] = a.z; u[4 * q + 3] = a.w;
+                x[4 * q] = c.x; x[4 * q + 1] = c.y; x[4 * q + 2] = c.z; x[4 * q + 3] = c.w;
+                jj[4 * q] = g.x; jj[4 * q + 1] = g.y; jj[4 * q + 2] = g.z; jj[4 * q + 3] = g.w;
+            }
+            // row of each entry (-1 outside [L0, L1))
+            int r = 0;
+            const int Lf = max(Lb, L0);
+            if (Lf < L1) {
+                int lo = 0, hi = nr - 1;                // largest r with off[r] <= Lf
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (R.off[mid] <= Lf) lo = mid; else hi = mid - 1;
+                }
+                r = lo;
+            }
+#pragma unroll
+            for (int k = 0; k < kTileE; k++) {
+                const int L = Lb + k;
+                if (L < L0 || L >= L1) {
+                    lr[k] = -1;
+                } else {
+                    while (R.off[r + 1] <= L) r++;
+                    lr[k] = r;
+                }
+                td[k] = 0.0f;
+                if (lr[k] >= 0) {
+                    const int j = jj[k];
+                    const float2 p = j < hot ? sp[j] : __ldg(bf.pff + j);
+                    ph[k] = p.x;
+                    pl[k] = p.y;
+                } else {
+                    u[k] = 0.0f; x[k] = 0.0f; ph[k] = 0.0f; pl[k] = 0.0f;
+                }
+            }
+        }
+
+        // ---- s0 = u^T x^k per row, float-float runs, FP64 combination ----
+        {
+            ff acc = ff_make(0.0f, 0.0f);
+            int rcur = -1;
+#pragma unroll
+            for (int k = 0; k < kTileE; k++) {
+                if (lr[k] < 0) continue;
+                if (lr[k] != rcur) {
+                    if (rcur >= 0) shared_add_f64(&R.s0[rcur], (double)acc.hi + (double)acc.lo);
+                    rcur = lr[k];
+                    acc = ff_make(0.0f, 0.0f);
+                }
+                acc = ff_add(acc, two_prod(u[k], x[k]));
+            }
+            seg_sum_ff(rcur, acc);
+            if (seg_head(rcur) && rcur >= 0) shared_add_f64(&R.s0[rcur], (double)acc.hi + (double)acc.lo);
+        }
+        __syncthreads();
+
+        // ---- start y_0 = w / s0 (float-float) ----
+        bool need = false;
+        if (tid < nr) {
+            const double s0 = R.s0[tid];
+            const ff y0 = ff_div(ff_from_double(sw[ro + tid]), ff_from_double(s0));
+            need = !(s0 > 0.0) || !(y0.hi > 0.0f) || !isfinite(y0.hi);
+            R.yh[tid] = y0.hi;
+            R.yl[tid] = y0.lo;
+            R.C[tid] = 0.0f;
+            R.A[tid] = 0.0f;
+            R.Q[tid] = 0.0f;
+        }
+        if (__syncthreads_or(need)) {
+            // x^k = 0 on a row: at y = max_j p_j / u_j every entry has d <= 0
+#pragma unroll
+            for (int k = 0; k < kTileE; k++)
+                if (lr[k] >= 0 && u[k] > 0.0f) shared_max_s32(&R.pmax[lr[k]], __float_as_int(ph[k] / u[k]));
+            __syncthreads();
+            if (need) {
+                const float pm = __int_as_float(R.pmax[tid]);
+                R.yh[tid] = pm > 0.0f ? pm : 1.0f;
+                R.yl[tid] = 0.0f;
+            }
+            __syncthreads();
+        }
+
+        // ---- evaluations and row updates until every row has converged ----
+        while (true) {
+            {
+                float cC = 0.0f, cA = 0.0f, cQ = 0.0f, yh = 0.0f, yl = 0.0f;
+                int rcur = -1;
+                bool act = false;
+#pragma unroll
+                for (int k = 0; k < kTileE; k++) {
+                    const int r = lr[k];
+                    if (r < 0) continue;
+                    if (r != rcur) {
+                        if (rcur >= 0 && act) {
+                            shared_add_f32(&R.C[rcur], cC);
+                            shared_add_f32(&R.A[rcur], cA);
+                            shared_add_f32(&R.Q[rcur], cQ);
+                        }
+                        rcur = r;
+                        cC = cA = cQ = 0.0f;
+                        act = !R.done[r];
+                        yh = R.yh[r];
+                        yl = R.yl[r];
+                    }
+                    if (!act) continue;
+                    const float uk = u[k];
+                    const float d = fmaf(-uk, yl, fmaf(-uk, yh, ph[k]) + pl[k]);
+                    const float tdk = tau * d;
+                    td[k] = tdk;
+                    const float cr = fminf(tdk, x[k]);
+                    cC = fmaf(uk, cr, cC);
+                    cA = fmaf(uk, fabsf(cr), cA);
+                    if (tdk < x[k]) cQ = fmaf(uk, uk, cQ);
+                }
+                const int key = (rcur >= 0 && act) ? rcur : -1;
+                seg_sum3(key, cC, cA, cQ);
+                if (seg_head(key) && key >= 0) {
+                    shared_add_f32(&R.C[key], cC);
+                    shared_add_f32(&R.A[key], cA);
+                    shared_add_f32(&R.Q[key], cQ);
+                }
+            }
+            __syncthreads();
+            bool more = false;
+            if (tid < nr && !R.done[tid]) {
+                const int r = tid;
+                const float yh = R.yh[r], yl = R.yl[r];
+                const float C = R.C[r], Ab = R.A[r], Q = R.Q[r];
+                R.C[r] = 0.0f;
+                R.A[r] = 0.0f;
+                R.Q[r] = 0.0f;
+                R.nev[r] += 1;
+                R.Clast[r] = C;
+                const ff s0 = ff_from_double(R.s0[r]);
+                const ff ws = ff_div(ff_from_double(sw[ro + r]), ff_make(yh, yl));     // w / y
+                const ff D = ff_sub(s0, ws);
+                const float F = (D.hi - C) + D.lo;
+                // rounding bound of F: per-thread runs of kTileE terms, a warp
+                // scan, one atomic per warp; plus the float-float resolution of
+                // p and y seen through tau Q y
+                const float deg = (float)(R.off[r + 1] - R.off[r]);
+                const float cn = 1.2e-7f * (2.83f + 5.0f + sqrtf(deg * (1.0f / 256.0f) + 1.0f));
+                const float aQ = tau * Q;
+                const float floor = fmaf(cn, Ab, fmaf(3e-14f, aQ * yh, 2e-8f * ws.hi));
+                const int steps = R.steps[r] + 1;
+                R.steps[r] = steps;
+                if (fabsf(F) <= floor || steps >= rc.cap) {
+                    R.done[r] = 1;
+                    if (fabsf(F) > floor) capped++;
+                } else {
+                    if (F > 0.0f) { R.hih[r] = yh; R.hil[r] = yl; } else { R.loh[r] = yh; R.lol[r] = yl; }
+                    const ff lo = ff_make(R.loh[r], R.lol[r]), hi = ff_make(R.hih[r], R.hil[r]);
+                    const float bq = fmaf(aQ, yh, F + ws.hi);
+                    const float cq = F * yh;
+                    const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
+                    const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
+                    ff yn = ff_add_f(ff_make(yh, yl), delta);
+                    if (!(ff_gt(yn, lo) && ff_gt(hi, yn)))
+                        yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
+                    if (yn.hi == yh && yn.lo == yl) {
+                        R.done[r] = 1;
+                    } else {
+                        R.yh[r] = yn.hi;
+                        R.yl[r] = yn.lo;
+                        more = true;
+                    }
+                }
+            }
+            if (!__syncthreads_or(more)) break;
+        }
+
+        // ---- utilities of the rows ----
+        if (tid < nr) {
+            bf.t[hd.ra + tid] = R.s0[tid] - (double)R.Clast[tid];
+            evals += R.nev[tid];
+        }
+
+        // ---- x^{k+1}, average fold, column sums ----
+        {
+            float xo[kTileE], xbo[kTileE];
+            if (rc.fold) {
+                const float4* b4 = (const float4*)(sxb + Lb);
+#pragma unroll
+                for (int q = 0; q < kTileE / 4; q++) {
+                    const float4 a = b4[q];
+                    xbo[4 * q] = a.x; xbo[4 * q + 1] = a.y; xbo[4 * q + 2] = a.z; xbo[4 * q + 3] = a.w;
+                }
+            }
+            // random bits: one mixed seed per thread and tile, then xorshift steps
+            unsigned rs = sr_bits(A0 + Lb, rc.seed) | 1u;
+#pragma unroll
+            for (int k = 0; k < kTileE; k++) {
+                xo[k] = 0.0f;
+                rs ^= rs << 13;
+                rs ^= rs >> 17;
+                rs ^= rs << 5;
+                if (lr[k] < 0) continue;
+                const unsigned rb = rs;
+                const float xn = td[k] < x[k] ? sr_add(x[k], -td[k], rb) : 0.0f;
+                xo[k] = xn;
+                const float dd = xn - x[k];
+                dxf = fmaf(dd, dd, dxf);
+                if (rc.fold) {
+                    const float xb = xbo[k];
+                    xbo[k] = (fw == 1.0f) ? x[k] : sr_add(xb, fw * (x[k] - xb), rb >> 16);
+                }
+                acc_add_fixed(acc_s, bf.acc, hot, jj[k], xn);
+            }
+            float* xg = Xout + A0 + Lb;
+            float* bg = Xb + A0 + Lb;
+            if (Lb >= L0 && Lb + kTileE <= L1) {
+#pragma unroll
+                for (int q = 0; q < kTileE / 4; q++) {
+                    __stcs((float4*)xg + q, make_float4(xo[4 * q], xo[4 * q + 1], xo[4 * q + 2], xo[4 * q + 3]));
+                    if (rc.fold) ((float4*)bg)[q] = make_float4(xbo[4 * q], xbo[4 * q + 1], xbo[4 * q + 2], xbo[4 * q + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kTileE; k++) {
+                    if (lr[k] < 0) continue;
+                    __stcs(xg + k, xo[k]);
+                    if (rc.fold) bg[k] = xbo[k];
+                }
+            }
+        }
+        __syncthreads();     // stage s and the row state are free again
+        s ^= 1;
+    }
+
+    if (timed_out) {
+        // a bulk copy never completed: report it, give the copies still in
+        // flight a bounded time to land, and leave without touching results
+        if (tid == 0) {
+            atomicExch(&ctl->nan_flag, 2);
+            mbar_wait(&bar[s], s ? par1 : par0);
+            if (t + (int)gridDim.x < mk.ntiles) mbar_wait(&bar[s ^ 1], s ? par0 : par1);
+        }
+        __syncthreads();
+        return;
+    }
+
+    // ---- rows longer than a tile: warp-chunked path ----
+    for (int bi = 0; bi < mk.nb; bi++) {
+        const Bucket bk = mk.buckets[bi];
+        const int lane = tid & 31;
+        while (true) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctl->work[bi], 1ull);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((long long)base >= bk.count) break;
+            const int row = mk.row_order[bk.first + (long long)base];
+            RowRegs Rg;
+            Rg.b = mk.rp[row];
+            Rg.e = mk.rp[row + 1];
+            row_mixed_core<32, true>(mk, (const float*)mk.uv, Xin, Xout, Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc, row,
+                                     true, dxf, capped, evals, Rg);
+        }
+    }
+
+    // ---- block epilogue: ||dx||^2 partial, counters, hot column sums ----
+    double v = warp_sum_d((double)dxf);
+    __shared__ double red[kWarps];
+    __shared__ int capred, evred;
+    if (tid == 0) capred = evred = 0;
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    if (capped) atomicAdd(&capred, capped);
+    if (evals) atomicAdd(&evred, evals);
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int w = 0; w < kWarps; w++) a += red[w];
+        bf.part[blockIdx.x] = a;
+        if (capred) atomicAdd((unsigned long long*)&ctl->capped, (unsigned long long)capred);
+        if (evred) atomicAdd((unsigned long long*)&ctl->evals, (unsigned long long)evred);
+    }
+    for (int j = tid; j < hot; j += kThreads) {
+        const unsigned long long a = acc_s[j];
+        if (a) atomicAdd(&bf.acc[j], a);
+    }
+}
+
+static void tile_attr() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+int tile_blocks(int hot) {
+    tile_attr();
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel, kThreads, tile_smem_bytes(hot));
+    const char* env = getenv("PDHCG_PROX_BLOCKS_PER_SM");
+    if (env && atoi(env) > 0 && atoi(env) < per) per = atoi(env);
+    return sm_count() * per;
+}
+
+void launch_tile(const DevMarket& mk, const IterBufs& b, Ctl* ctl, const void* x_in, void* x_out, int fixed,
+                 cudaStream_t s) {
+    tile_attr();
+    tile_kernel<<<mk.nprox, kThreads, tile_smem_bytes(mk.hot), s>>>(mk, x_in, x_out, b, ctl, fixed);
+}
+
+}  // namespace pdhcg
