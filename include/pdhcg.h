@@ -95,7 +95,8 @@ typedef struct {
     int32_t omega_reset_every; /* 3    restarts between primal-weight range checks  */
     double omega_range;        /* 100  allowed range omega_0 / r .. omega_0 * r     */
     int32_t row_solve_max_iter;/* cap on active-set rounds of one row solve (64)    */
-    double tight_kappa;        /* relative slack defining tight edges (backward)    */
+    double tight_kappa;        /* relative slack defining tight edges (backward);
+                                  0: 100 x the KKT error reached, in [1e-9, 1e-3]   */
     int32_t verbose;           /* 0 silent, 1 one line per check to stderr          */
     int32_t timing;            /* 1: time every row-kernel launch with CUDA events
                                   (fills pdhcg_info.prox_ms / prox_launches)        */
@@ -133,7 +134,7 @@ int32_t pdhcg_version(void);      /* major * 100 + minor */
 /* Defaults: tol 1e-6, max_iter 1e6, time limit 1e9 s, MIXED, check every 64,
  * betas 0.2/0.8/0.2 and theta 0.2 (Section 5), eta in [0.01, 3] eta_0
  * (Section 5), eta0_scale 0.9, omega reset every 3 restarts (Section 5),
- * omega_range 100, 64 row-solve rounds, tight_kappa 1e-5. */
+ * omega_range 100, 64 row-solve rounds, tight_kappa 0 (automatic). */
 void pdhcg_default_params(pdhcg_params* prm);
 
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*) on the

@@ -60,9 +60,15 @@ __global__ void tight_kernel(AdjArgs a, int* ei, int* ej, long long* eq, unsigne
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long i = gw; i < a.n; i += nw) {
         const double y = a.w[i] / a.t[i];
+        // support: x_ij above 1e-9 of the row's largest allocation (first-order
+        // iterates keep vanishing entries slightly positive for a while)
+        double xm = 0.0;
+        for (long long q = a.rp[i] + lane; q < a.rp[i + 1]; q += 32)
+            xm = fmax(xm, a.f32 ? (double)((const float*)a.x)[q] : ((const double*)a.x)[q]);
+        xm = warp_max_d(xm);
         for (long long q = a.rp[i] + lane; q < a.rp[i + 1]; q += 32) {
             const double x = a.f32 ? (double)((const float*)a.x)[q] : ((const double*)a.x)[q];
-            if (!(x > 0.0)) continue;
+            if (!(x > 1e-9 * xm)) continue;
             const double u = a.f32 ? (double)((const float*)a.uv)[q] : ((const double*)a.uv)[q];
             const int j = a.cj[q];
             if (a.p[j] <= u * y * (1.0 + a.kappa)) {
@@ -130,9 +136,9 @@ __global__ void degree_kernel(int ne, int n, const int* ei, const int* ej, doubl
 
 // ---- CG pieces (scalars stay on the device) ----
 struct CgScal {
-    double rz, rz_new, pq, alpha, beta, rr, bb;
+    double rz, rz_new, pq, alpha, beta, rr, bb, rz0;
     unsigned int ticket;
-    int pad;
+    int stop;               // converged: further iterations leave z unchanged
 };
 __global__ void lap_kernel(int ne, int n, const int* ei, const int* ej, const double* z, double* y) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
@@ -162,17 +168,22 @@ __device__ void finish_dot(double v, double* part, CgScal* S, int which) {
     double s = 0.0;
     for (int b = 0; b < (int)gridDim.x; b++) s += ((volatile double*)part)[b];
     S->ticket = 0u;
+    // iterations run in fixed-size graphs, so the ones after convergence must
+    // leave the solution alone instead of dividing rounding noise by itself
     if (which == 0) {            // p . q  ->  alpha
         S->pq = s;
-        S->alpha = s != 0.0 ? S->rz / s : 0.0;
+        S->alpha = (!S->stop && s > 0.0) ? S->rz / s : 0.0;
     } else if (which == 1) {     // r . z_new -> beta
         S->rz_new = s;
-        S->beta = S->rz != 0.0 ? s / S->rz : 0.0;
+        if (!(s > 1e-26 * S->rz0)) S->stop = 1;
+        S->beta = (!S->stop && S->rz > 0.0) ? s / S->rz : 0.0;
         S->rz = s;
     } else if (which == 2) {     // r . r
         S->rr = s;
     } else {                     // initial r . z
         S->rz = s;
+        S->rz0 = s;
+        S->stop = !(s > 0.0);
     }
 }
 __global__ void dot_pq_kernel(int nv, const double* p, const double* q, double* part, CgScal* S) {
@@ -276,7 +287,8 @@ __global__ void ad_step_kernel(int nv, const int* label, const int* cl, const do
         atomicAdd(&csum[cl[v]], P[v] * nl);
     }
 }
-// projection per class and the largest change (as bits of a non-negative double)
+// projection per class; the largest change and the largest |lambda| (as bits
+// of non-negative doubles, dmax[0] and dmax[1])
 __global__ void ad_project_kernel(int nv, const int* label, const int* cl, const double* PPc, const double* csum,
                                   double* lam_new, const double* lam, unsigned long long* dmax) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
@@ -285,7 +297,8 @@ __global__ void ad_project_kernel(int nv, const int* label, const int* cl, const
         const double nl = lam_new[v] - csum[c] / PPc[c];
         lam_new[v] = nl;
         const double d = fabs(nl - lam[v]);
-        if (d > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(d));
+        if (d > 0.0) atomicMax(&dmax[0], (unsigned long long)__double_as_longlong(d));
+        if (nl != 0.0) atomicMax(&dmax[1], (unsigned long long)__double_as_longlong(fabs(nl)));
     }
 }
 __global__ void ad_pi_kernel(int n, int m, const int* label, const double* p, const double* P, const double* rt,
@@ -316,6 +329,15 @@ __global__ void ad_mu_kernel(int n, int m, const int* label, const int* agent_ro
 using namespace pdhcg;
 
 namespace {
+
+// Slack of the tight-edge test: the caller's, else 100 x the KKT error the
+// solve reached (within [1e-9, 1e-3]): support edges are tight to about the
+// KKT error, and edges that are tight only to within a wider margin belong to
+// a different (nearby) equilibrium structure.
+double eff_kappa(double user, double kkt) {
+    if (user > 0.0) return user;
+    return std::min(1e-3, std::max(1e-9, 100.0 * kkt));
+}
 
 int gsz(long long n) {
     long long b = (n + 255) / 256;
@@ -417,7 +439,7 @@ pdhcg_status adjoint_core(pdhcg_handle h, const AdjArgs& a, const double* r, con
                 return PDHCG_ERR_CUDA;
             }
             res = std::sqrt(h->host->kout[0].r_primal / bnorm2);
-            if (!(res > 1e-12)) break;
+            if (!(res > 1e-10)) break;
         }
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
@@ -493,7 +515,7 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
         a.x = h->bt[18].p;
         a.p = (const double*)h->bt[22].p;
         a.t = (const double*)h->bt[23].p;
-        a.kappa = h->tight_kappa;
+        a.kappa = eff_kappa(h->tight_kappa, h->bt_kkt_max);
         double res;
         int ne, kc;
         pdhcg_status r = adjoint_core(h, a, gp, gt, gu, gw, 200000, &res, &ne, &kc, nullptr);
@@ -539,7 +561,7 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
     a.x = R.x;
     a.p = R.p;
     a.t = R.t;
-    a.kappa = h->tight_kappa;
+    a.kappa = eff_kappa(h->tight_kappa, R.kkt.kkt);
     if (st.kind == 1) {
         // ---- Arrow-Debreu: replace r by mu (see the file comment) ----
         const int nv = n + m;
@@ -557,7 +579,7 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
         double* csum = base + 6 * (size_t)nv;     // by class root
         double* PPc = base + 7 * (size_t)nv;      // by class root (also RP during centring)
         unsigned long long* dmax = (unsigned long long*)B[14].p;
-        int* changed = (int*)((char*)B[14].p + 8);
+        int* changed = (int*)((char*)B[14].p + 16);
         int* cl = (int*)B[16].p;
         // components of the tight graph (one derivative pass computes them)
         double res0;
@@ -598,17 +620,17 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
         cudaGraph_t graph;
         cudaGraphExec_t exec;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        cudaMemsetAsync(dmax, 0, 8, s);
+        cudaMemsetAsync(dmax, 0, 16, s);
         for (int k = 0; k < 16; k++) {
             cudaMemsetAsync(qlam, 0, (size_t)nv * sizeof(double), s);
             cudaMemsetAsync(csum, 0, (size_t)nv * sizeof(double), s);
             ad_q_kernel<<<gsz(m), 256, 0, s>>>(n, m, label, agent_row, pi, lam, qlam);
             ad_step_kernel<<<gsz(nv), 256, 0, s>>>(nv, label, cl, Pc, rho, qlam, lam, lamn, csum);
-            if (k == 15) cudaMemsetAsync(dmax, 0, 8, s);
+            if (k == 15) cudaMemsetAsync(dmax, 0, 16, s);
             ad_project_kernel<<<gsz(nv), 256, 0, s>>>(nv, label, cl, PPc, csum, lamn, lam, dmax);
             cudaMemcpyAsync(lam, lamn, (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
         }
-        cudaMemcpyAsync(&h->host->kout[0], dmax, 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&h->host->kout[0], dmax, 16, cudaMemcpyDeviceToHost, s);
         CK(cudaStreamEndCapture(s, &graph));
         CK(cudaGraphInstantiate(&exec, graph, 0));
         bool ok = false;
@@ -616,9 +638,11 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
             cudaError_t ce = cudaGraphLaunch(exec, s);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (note_error(ce, "adjoint fixed point") != cudaSuccess) break;
-            double d;
+            double d, lmax;
             memcpy(&d, &h->host->kout[0], 8);
-            if (!(d > 1e-14)) { ok = true; break; }
+            memcpy(&lmax, (const char*)&h->host->kout[0] + 8, 8);
+            // the last step changed lambda by at most 1e-13 of its size
+            if (!(d > 1e-13 * std::max(1.0, lmax))) { ok = true; break; }
         }
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);

@@ -903,5 +903,7 @@ pdhcg_status pdhcg_fisher_solve_batched(pdhcg_handle h, int32_t B, const int64_t
     h->bt_NNZ = NNZ;
     h->bt_mixed = mixed;
     h->tight_kappa = prm->tight_kappa;
+    h->bt_kkt_max = 0.0;
+    for (int b = 0; b < B; b++) h->bt_kkt_max = std::max(h->bt_kkt_max, st[b].kkt);
     return all;
 }

@@ -34,7 +34,7 @@ constexpr int kSlots = 4;                               // entries per lane held
 constexpr int kTileE = 8;
 constexpr int kTileCap = kThreads * kTileE;             // entries per tile (from the 4-aligned start)
 constexpr int kTileRows = 128;                          // rows per tile
-constexpr int kTileHotMax = 2048;                       // hot goods staged in shared memory
+constexpr int kTileHotMax = 3072;                       // hot goods staged in shared memory
 constexpr int kPadEntries = 16;                         // slack after nnz arrays read by bulk copies
 
 // ---------------------------------------------------------------------------

@@ -341,7 +341,7 @@ static pdhcg_status alloc_iter(pdhcg_handle h) {
     for (DevBuf* b : gv) CK(ensure(*b, m * sizeof(double)));
     CK(ensure(h->pff, m * sizeof(float2)));
     CK(ensure(h->acc, 3 * (size_t)m * sizeof(unsigned long long)));
-    CK(ensure(h->t, n * sizeof(double)));
+    CK(ensure(h->t, (n + 2) * sizeof(double)));   // +2: read by 16-byte bulk copies
     CK(ensure(h->t_cur, n * sizeof(double)));
     CK(ensure(h->t_avg, n * sizeof(double)));
     CK(ensure(h->part, std::max(max_prox_blocks(), dist_blocks()) * sizeof(double)));
@@ -471,6 +471,8 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
     // initial column sums and KKT of the starting point
     KktBufs kc = kkt_bufs(h, (double*)h->c_cur.p, (double*)h->t_cur.p, 0);
     launch_kkt(mixed, P.dm, h->X0.p, (const double*)h->p.p, kc, s);
+    // utilities of the starting point: the row kernel's warm start y_0 = w / t
+    CK(cudaMemcpyAsync(h->t.p, h->t_cur.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->C0.p, h->c_cur.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->C1.p, h->c_cur.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(&h->host->kout[0], h->kout.p, sizeof(KktOut), cudaMemcpyDeviceToHost, s));
@@ -604,6 +606,7 @@ pdhcg_status session_step(pdhcg_handle h, long long chunks) {
             }
             CK(cudaMemcpyAsync(Cbuf[c.ck], csrc, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
             CK(cudaMemcpyAsync(Cbuf[c.ckm1], csrc, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(h->t.p, h->t_cur.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
             // distances to the previous restart point, then remember this one
             const int nb = dist_blocks();
             std::vector<double> pa(nb), pb(nb);
@@ -717,7 +720,7 @@ void pdhcg_default_params(pdhcg_params* p) {
     p->omega_reset_every = 3;
     p->omega_range = 100.0;
     p->row_solve_max_iter = 64;
-    p->tight_kappa = 1e-5;
+    p->tight_kappa = 0.0;
     p->verbose = 0;
 }
 
@@ -923,6 +926,8 @@ pdhcg_status pdhcg_row_prox(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precis
         CK(cudaMemcpyAsync(h->X1.p, xi, P.nnz * vb, cudaMemcpyDeviceToDevice, s));
         xk = h->X1.p;
         xw = h->Xr.p;
+        // warm start of the row solve: t = u^T x_in
+        k_row_dot_f32(P.n, (const long long*)P.dm.rp, (const float*)P.dm.uv, (const float*)xk, (double*)h->t.p, s);
     }
     launch_prox_fixed(mixed, P.dm, xk, xw, (const double*)h->p0i.p, tau, (unsigned long long*)h->acc.p,
                       (double*)h->t.p, (double*)h->c_cur.p, (double*)h->part.p, (Ctl*)h->ctl.p, s);

@@ -128,8 +128,9 @@ struct pdhcg_handle_s {
     int bt_N = 0, bt_M = 0;           // sizes of the last batched solve (for backward)
     long long bt_NNZ = 0;
     bool bt_mixed = true;
-    double tight_kappa = 1e-5;
-    pdhcg::DevBuf adj[16];
+    double tight_kappa = 0.0;   // 0: automatic (from the KKT error of the solve)
+    double bt_kkt_max = 0.0;    // largest KKT error of the last batched solve
+    pdhcg::DevBuf adj[24];
     pdhcg::HostMirror* host = nullptr;
 
     void release() {

@@ -5,16 +5,19 @@
 // Buyers are cut, in CSR order, into tiles of whole rows holding at most
 // kTileCap entries and kTileRows rows.  A persistent block takes every
 // gridDim.x-th tile.  A tile's utilities, x^k, x-bar and good ids, with its
-// row offsets and budgets, arrive by bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier) in one of two shared-memory
-// stages, so the next tile streams in while the current one is solved.  Each
-// thread owns kTileE consecutive entries of the tile.  Row sums are per-thread
-// runs combined by a segmented warp scan and shared-memory atomics, and the
-// row equations of all rows of the tile are iterated together: one evaluation
-// is one sweep over the tile's entries followed by one update per row, until
-// every row has converged.  The arithmetic is that of row_mixed_core: s0 and
-// w/y in float-float, FP32 corrections C = sum u min(tau d, x), the
-// frozen-active-set quadratic step, stochastic rounding of x^{k+1} and x-bar.
+// row offsets, budgets and the utilities t of the previous pass, arrive by
+// bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) in one
+// of two shared-memory stages, so the next tile streams in while the current
+// one is solved.  Each thread owns kTileE consecutive entries.  Row sums are
+// per-thread runs combined by a segmented warp scan and shared-memory atomics.
+//
+// Row equation (the arithmetic of row_mixed_core): F(y) = s0 - C(y) - w/y with
+// s0 = u^T x^k and w/y in float-float and C(y) = sum u min(tau d, x) in FP32.
+// Every row starts from y_0 = w / t_prev, so the first sweep computes s0 and
+// the evaluation at y_0 together.  A frozen-active-set quadratic step then
+// gives y_1; when no entry of the row changes activity between y_0 and y_1
+// the frozen model is exact and y_1 is the root, which a sweep without
+// reductions verifies.  Only rows whose active set moved are evaluated again.
 // Rows longer than a tile go to the warp-chunked path after the tiles.
 #include <cstdlib>
 
@@ -33,7 +36,8 @@ constexpr int kOffXb = kOffX + kTileCap * 4;
 constexpr int kOffJ = kOffXb + kTileCap * 4;
 constexpr int kOffRp = kOffJ + kTileCap * 4;
 constexpr int kOffW = kOffRp + kTileRowBuf * 8;
-constexpr int kStageBytes = kOffW + kTileRowBuf * 8;
+constexpr int kOffT = kOffW + kTileRowBuf * 8;
+constexpr int kStageBytes = kOffT + kTileRowBuf * 8;
 static_assert(kStageBytes % 16 == 0, "stage size must keep 16-byte alignment");
 static_assert(kTileCap == kThreads * kTileE, "tile capacity");
 
@@ -43,13 +47,16 @@ struct TileHdr {
 };
 
 // per-row state of the tile being solved
+enum : int { kRowEval = 0, kRowCheck = 1, kRowDone = 2 };
 struct TileRows {
     double s0[kTileRows];
-    float yh[kTileRows], yl[kTileRows];
+    double Cf[kTileRows];           // C at the final y (utility t = s0 - Cf)
+    float yh[kTileRows], yl[kTileRows];            // current y
+    float ymh[kTileRows], yml[kTileRows];          // point of the frozen model (state kRowCheck)
     float loh[kTileRows], lol[kTileRows], hih[kTileRows], hil[kTileRows];
-    float C[kTileRows], A[kTileRows], Q[kTileRows], Clast[kTileRows];
-    int pmax[kTileRows];            // max_j p_j / u_j as float bits (start of an empty row)
-    int steps[kTileRows], nev[kTileRows], done[kTileRows];
+    float C[kTileRows], A[kTileRows], Q[kTileRows];
+    float Cm[kTileRows], Qm[kTileRows];            // C and Q of the frozen model
+    int st[kTileRows], chg[kTileRows], steps[kTileRows], nev[kTileRows];
     int off[kTileRows + 1];         // entry offsets of the rows, relative to A
 };
 
@@ -92,13 +99,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void shared_add_f32(float* p, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(p)), "f"(v) : "memory");
 }
-__device__ __forceinline__ void shared_max_s32(int* p, int v) {
-    asm volatile("red.shared.max.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
-}
 
 // thread 0: start the copies of tile t into a stage
-__device__ void tile_issue(const DevMarket& mk, const float* Xin, const float* Xb, bool fold, int t,
-                           unsigned char* st, unsigned long long* bar, TileHdr* hd) {
+__device__ void tile_issue(const DevMarket& mk, const float* Xin, const float* Xb, const double* tprev, bool fold,
+                           int t, unsigned char* st, unsigned long long* bar, TileHdr* hd) {
     const int2 rr = mk.tile_rows[t];
     const longlong2 ee = mk.tile_ent[t];
     const long long A = ee.x & ~3LL;
@@ -111,7 +115,7 @@ __device__ void tile_issue(const DevMarket& mk, const float* Xin, const float* X
     hd->A = A;
     hd->ra = rr.x;
     hd->rb = rr.y;
-    const unsigned bytes = vb * (fold ? 4u : 3u) + (nrp + nw) * 8u;
+    const unsigned bytes = vb * (fold ? 4u : 3u) + (nrp + 2 * nw) * 8u;
     proxy_fence();
     mbar_expect_tx(bar, bytes);
     bulk_g2s(st + kOffU, (const float*)mk.uv + A, vb, bar);
@@ -120,6 +124,7 @@ __device__ void tile_issue(const DevMarket& mk, const float* Xin, const float* X
     bulk_g2s(st + kOffJ, mk.cj + A, vb, bar);
     bulk_g2s(st + kOffRp, mk.rp + ra2, nrp * 8u, bar);
     bulk_g2s(st + kOffW, mk.w + ra2, nw * 8u, bar);
+    bulk_g2s(st + kOffT, tprev + ra2, nw * 8u, bar);
 }
 
 // Segmented suffix sums over the lanes of a warp: lanes with equal keys form
@@ -153,7 +158,9 @@ __device__ __forceinline__ void seg_sum_ff(int key, ff& v) {
 
 }  // namespace
 
-size_t tile_smem_bytes(int hot) { return (size_t)hot * 16 + 2 * (size_t)kStageBytes; }
+// hot column sums, then the two stages (16-byte aligned for the bulk copies and vector reads)
+__host__ __device__ static inline size_t stage_offset(int hot) { return ((size_t)hot * 8 + 15) & ~(size_t)15; }
+size_t tile_smem_bytes(int hot) { return stage_offset(hot) + 2 * (size_t)kStageBytes; }
 
 __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const void* Xin_fixed, void* Xout_fixed,
                                                          IterBufs bf, Ctl* ctl, int fixed) {
@@ -181,12 +188,8 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
     const int hot = mk.hot;
 
     unsigned long long* acc_s = (unsigned long long*)smem;
-    float2* sp = (float2*)(acc_s + hot);
-    unsigned char* stages = smem + (size_t)hot * 16;
-    for (int j = tid; j < hot; j += kThreads) {
-        acc_s[j] = 0ull;
-        sp[j] = bf.pff[j];
-    }
+    unsigned char* stages = smem + stage_offset(hot);
+    for (int j = tid; j < hot; j += kThreads) acc_s[j] = 0ull;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -200,12 +203,12 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
     bool timed_out = false;
     int s = 0;
     int t = blockIdx.x;
-    if (tid == 0 && t < mk.ntiles) tile_issue(mk, Xin, Xb, rc.fold, t, stages, &bar[0], &hdr[0]);
+    if (tid == 0 && t < mk.ntiles) tile_issue(mk, Xin, Xb, bf.t, rc.fold, t, stages, &bar[0], &hdr[0]);
 
     for (; t < mk.ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
         if (tid == 0 && tn < mk.ntiles)
-            tile_issue(mk, Xin, Xb, rc.fold, tn, stages + (size_t)(s ^ 1) * kStageBytes, &bar[s ^ 1], &hdr[s ^ 1]);
+            tile_issue(mk, Xin, Xb, bf.t, rc.fold, tn, stages + (size_t)(s ^ 1) * kStageBytes, &bar[s ^ 1], &hdr[s ^ 1]);
         const bool ok = mbar_wait(&bar[s], s ? par1 : par0);
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (s) par1 ^= 1u; else par0 ^= 1u;
@@ -218,19 +221,30 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
         const int* sj = (const int*)(st + kOffJ);
         const long long* srp = (const long long*)(st + kOffRp);
         const double* sw = (const double*)(st + kOffW);
+        const double* stp = (const double*)(st + kOffT);
         const TileHdr hd = hdr[s];
         const int nr = hd.rb - hd.ra;
         const long long A0 = hd.A;
         const int ro = hd.ra & 1;
         const int L0 = (int)(hd.ea - A0), L1 = (int)(hd.eb - A0);
 
+        // ---- rows: offsets and the start y_0 = w / t_prev ----
         if (tid <= nr) R.off[tid] = (int)(srp[ro + tid] - A0);
         if (tid < nr) {
+            const double tp = stp[ro + tid];
+            ff y0 = ff_make(1.0f, 0.0f);
+            if (tp > 0.0 && tp < 1e300) y0 = ff_div(ff_from_double(sw[ro + tid]), ff_from_double(tp));
+            if (!(y0.hi > 0.0f) || !isfinite(y0.hi)) y0 = ff_make(1.0f, 0.0f);
+            R.yh[tid] = y0.hi;
+            R.yl[tid] = y0.lo;
             R.s0[tid] = 0.0;
-            R.pmax[tid] = 0;
+            R.C[tid] = 0.0f;
+            R.A[tid] = 0.0f;
+            R.Q[tid] = 0.0f;
+            R.st[tid] = kRowEval;
+            R.chg[tid] = 0;
             R.steps[tid] = 0;
             R.nev[tid] = 0;
-            R.done[tid] = 0;
             R.loh[tid] = 0.0f;
             R.lol[tid] = 0.0f;
             R.hih[tid] = INFINITY;
@@ -242,6 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
         const int Lb = tid * kTileE;
         float u[kTileE], x[kTileE], ph[kTileE], pl[kTileE], td[kTileE];
         int lr[kTileE], jj[kTileE];
+        unsigned actm = 0u;           // bit k: entry k active (tau d < x) at the last evaluation
         {
             const float4* u4 = (const float4*)(su + Lb);
             const float4* x4 = (const float4*)(sx + Lb);
@@ -254,7 +269,6 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
                 x[4 * q] = c.x; x[4 * q + 1] = c.y; x[4 * q + 2] = c.z; x[4 * q + 3] = c.w;
                 jj[4 * q] = g.x; jj[4 * q + 1] = g.y; jj[4 * q + 2] = g.z; jj[4 * q + 3] = g.w;
             }
-            // row of each entry (-1 outside [L0, L1))
             int r = 0;
             const int Lf = max(Lb, L0);
             if (Lf < L1) {
@@ -268,161 +282,168 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
 #pragma unroll
             for (int k = 0; k < kTileE; k++) {
                 const int L = Lb + k;
+                td[k] = 0.0f;
                 if (L < L0 || L >= L1) {
                     lr[k] = -1;
+                    u[k] = 0.0f; x[k] = 0.0f; ph[k] = 0.0f; pl[k] = 0.0f;
                 } else {
                     while (R.off[r + 1] <= L) r++;
                     lr[k] = r;
-                }
-                td[k] = 0.0f;
-                if (lr[k] >= 0) {
-                    const int j = jj[k];
-                    const float2 p = j < hot ? sp[j] : __ldg(bf.pff + j);
+                    const float2 p = __ldg(bf.pff + jj[k]);
                     ph[k] = p.x;
                     pl[k] = p.y;
-                } else {
-                    u[k] = 0.0f; x[k] = 0.0f; ph[k] = 0.0f; pl[k] = 0.0f;
                 }
             }
         }
 
-        // ---- s0 = u^T x^k per row, float-float runs, FP64 combination ----
-        {
-            ff acc = ff_make(0.0f, 0.0f);
-            int rcur = -1;
-#pragma unroll
-            for (int k = 0; k < kTileE; k++) {
-                if (lr[k] < 0) continue;
-                if (lr[k] != rcur) {
-                    if (rcur >= 0) shared_add_f64(&R.s0[rcur], (double)acc.hi + (double)acc.lo);
-                    rcur = lr[k];
-                    acc = ff_make(0.0f, 0.0f);
-                }
-                acc = ff_add(acc, two_prod(u[k], x[k]));
-            }
-            seg_sum_ff(rcur, acc);
-            if (seg_head(rcur) && rcur >= 0) shared_add_f64(&R.s0[rcur], (double)acc.hi + (double)acc.lo);
-        }
-        __syncthreads();
-
-        // ---- start y_0 = w / s0 (float-float) ----
-        bool need = false;
-        if (tid < nr) {
-            const double s0 = R.s0[tid];
-            const ff y0 = ff_div(ff_from_double(sw[ro + tid]), ff_from_double(s0));
-            need = !(s0 > 0.0) || !(y0.hi > 0.0f) || !isfinite(y0.hi);
-            R.yh[tid] = y0.hi;
-            R.yl[tid] = y0.lo;
-            R.C[tid] = 0.0f;
-            R.A[tid] = 0.0f;
-            R.Q[tid] = 0.0f;
-        }
-        if (__syncthreads_or(need)) {
-            // x^k = 0 on a row: at y = max_j p_j / u_j every entry has d <= 0
-#pragma unroll
-            for (int k = 0; k < kTileE; k++)
-                if (lr[k] >= 0 && u[k] > 0.0f) shared_max_s32(&R.pmax[lr[k]], __float_as_int(ph[k] / u[k]));
-            __syncthreads();
-            if (need) {
-                const float pm = __int_as_float(R.pmax[tid]);
-                R.yh[tid] = pm > 0.0f ? pm : 1.0f;
-                R.yl[tid] = 0.0f;
-            }
-            __syncthreads();
-        }
-
-        // ---- evaluations and row updates until every row has converged ----
+        // ---- sweeps: s0 (first sweep only), evaluations, activity checks ----
+        bool first = true;
         while (true) {
             {
+                ff sacc = ff_make(0.0f, 0.0f);
                 float cC = 0.0f, cA = 0.0f, cQ = 0.0f, yh = 0.0f, yl = 0.0f;
-                int rcur = -1;
-                bool act = false;
+                int rcur = -1, rst = kRowDone;
+                bool chg = false;
 #pragma unroll
                 for (int k = 0; k < kTileE; k++) {
                     const int r = lr[k];
                     if (r < 0) continue;
                     if (r != rcur) {
-                        if (rcur >= 0 && act) {
-                            shared_add_f32(&R.C[rcur], cC);
-                            shared_add_f32(&R.A[rcur], cA);
-                            shared_add_f32(&R.Q[rcur], cQ);
+                        if (rcur >= 0) {
+                            if (first) shared_add_f64(&R.s0[rcur], (double)sacc.hi + (double)sacc.lo);
+                            if (rst == kRowEval) {
+                                shared_add_f32(&R.C[rcur], cC);
+                                shared_add_f32(&R.A[rcur], cA);
+                                shared_add_f32(&R.Q[rcur], cQ);
+                            } else if (rst == kRowCheck && chg) {
+                                atomicOr(&R.chg[rcur], 1);
+                            }
                         }
                         rcur = r;
-                        cC = cA = cQ = 0.0f;
-                        act = !R.done[r];
+                        rst = R.st[r];
                         yh = R.yh[r];
                         yl = R.yl[r];
+                        sacc = ff_make(0.0f, 0.0f);
+                        cC = cA = cQ = 0.0f;
+                        chg = false;
                     }
-                    if (!act) continue;
+                    if (first) sacc = ff_add(sacc, two_prod(u[k], x[k]));
+                    if (rst == kRowDone) continue;
                     const float uk = u[k];
                     const float d = fmaf(-uk, yl, fmaf(-uk, yh, ph[k]) + pl[k]);
                     const float tdk = tau * d;
                     td[k] = tdk;
-                    const float cr = fminf(tdk, x[k]);
-                    cC = fmaf(uk, cr, cC);
-                    cA = fmaf(uk, fabsf(cr), cA);
-                    if (tdk < x[k]) cQ = fmaf(uk, uk, cQ);
+                    const bool act = tdk < x[k];
+                    const unsigned bit = 1u << k;
+                    if (rst == kRowCheck) {
+                        chg |= act != ((actm & bit) != 0u);
+                    } else {
+                        const float cr = fminf(tdk, x[k]);
+                        cC = fmaf(uk, cr, cC);
+                        cA = fmaf(uk, fabsf(cr), cA);
+                        if (act) cQ = fmaf(uk, uk, cQ);
+                    }
+                    actm = act ? (actm | bit) : (actm & ~bit);
                 }
-                const int key = (rcur >= 0 && act) ? rcur : -1;
+                if (first) {
+                    seg_sum_ff(rcur, sacc);
+                    if (seg_head(rcur) && rcur >= 0) shared_add_f64(&R.s0[rcur], (double)sacc.hi + (double)sacc.lo);
+                }
+                const int key = (rcur >= 0 && rst == kRowEval) ? rcur : -1;
                 seg_sum3(key, cC, cA, cQ);
                 if (seg_head(key) && key >= 0) {
                     shared_add_f32(&R.C[key], cC);
                     shared_add_f32(&R.A[key], cA);
                     shared_add_f32(&R.Q[key], cQ);
                 }
+                if (rcur >= 0 && rst == kRowCheck && chg) atomicOr(&R.chg[rcur], 1);
             }
             __syncthreads();
-            bool more = false;
-            if (tid < nr && !R.done[tid]) {
+            first = false;
+            bool pending = false;
+            if (tid < nr) {
                 const int r = tid;
-                const float yh = R.yh[r], yl = R.yl[r];
-                const float C = R.C[r], Ab = R.A[r], Q = R.Q[r];
-                R.C[r] = 0.0f;
-                R.A[r] = 0.0f;
-                R.Q[r] = 0.0f;
-                R.nev[r] += 1;
-                R.Clast[r] = C;
-                const ff s0 = ff_from_double(R.s0[r]);
-                const ff ws = ff_div(ff_from_double(sw[ro + r]), ff_make(yh, yl));     // w / y
-                const ff D = ff_sub(s0, ws);
-                const float F = (D.hi - C) + D.lo;
-                // rounding bound of F: per-thread runs of kTileE terms, a warp
-                // scan, one atomic per warp; plus the float-float resolution of
-                // p and y seen through tau Q y
-                const float deg = (float)(R.off[r + 1] - R.off[r]);
-                const float cn = 1.2e-7f * (2.83f + 5.0f + sqrtf(deg * (1.0f / 256.0f) + 1.0f));
-                const float aQ = tau * Q;
-                const float floor = fmaf(cn, Ab, fmaf(3e-14f, aQ * yh, 2e-8f * ws.hi));
-                const int steps = R.steps[r] + 1;
-                R.steps[r] = steps;
-                if (fabsf(F) <= floor || steps >= rc.cap) {
-                    R.done[r] = 1;
-                    if (fabsf(F) > floor) capped++;
-                } else {
-                    if (F > 0.0f) { R.hih[r] = yh; R.hil[r] = yl; } else { R.loh[r] = yh; R.lol[r] = yl; }
-                    const ff lo = ff_make(R.loh[r], R.lol[r]), hi = ff_make(R.hih[r], R.hil[r]);
-                    const float bq = fmaf(aQ, yh, F + ws.hi);
-                    const float cq = F * yh;
-                    const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
-                    const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
-                    ff yn = ff_add_f(ff_make(yh, yl), delta);
-                    if (!(ff_gt(yn, lo) && ff_gt(hi, yn)))
-                        yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
-                    if (yn.hi == yh && yn.lo == yl) {
-                        R.done[r] = 1;
+                const int rs = R.st[r];
+                if (rs == kRowCheck) {
+                    if (!R.chg[r]) {
+                        // active set unchanged: the frozen model is exact at y
+                        const double dy = ((double)R.yh[r] - (double)R.ymh[r]) + ((double)R.yl[r] - (double)R.yml[r]);
+                        R.Cf[r] = (double)R.Cm[r] - (double)tau * (double)R.Qm[r] * dy;
+                        R.st[r] = kRowDone;
                     } else {
-                        R.yh[r] = yn.hi;
-                        R.yl[r] = yn.lo;
-                        more = true;
+                        R.chg[r] = 0;
+                        R.st[r] = kRowEval;
+                        pending = true;
+                    }
+                } else if (rs == kRowEval) {
+                    const float yh = R.yh[r], yl = R.yl[r];
+                    const float C = R.C[r], Ab = R.A[r], Q = R.Q[r];
+                    R.C[r] = 0.0f;
+                    R.A[r] = 0.0f;
+                    R.Q[r] = 0.0f;
+                    R.nev[r] += 1;
+                    const ff s0 = ff_from_double(R.s0[r]);
+                    const ff ws = ff_div(ff_from_double(sw[ro + r]), ff_make(yh, yl));     // w / y
+                    const ff D = ff_sub(s0, ws);
+                    const float F = (D.hi - C) + D.lo;
+                    // rounding bound of F: per-thread runs of kTileE terms, a warp
+                    // scan, one atomic per warp; plus the float-float resolution of
+                    // p and y seen through tau Q y
+                    const float deg = (float)(R.off[r + 1] - R.off[r]);
+                    const float cn = 1.2e-7f * (2.83f + 5.0f + sqrtf(deg * (1.0f / 256.0f) + 1.0f));
+                    const float aQ = tau * Q;
+                    const float floor = fmaf(cn, Ab, fmaf(3e-14f, aQ * yh, 2e-8f * ws.hi));
+                    const int steps = R.steps[r] + 1;
+                    R.steps[r] = steps;
+                    bool fin = false;
+                    if (fabsf(F) <= floor || steps >= rc.cap) {
+                        fin = true;
+                        if (fabsf(F) > floor) capped++;
+                    } else {
+                        if (F > 0.0f) { R.hih[r] = yh; R.hil[r] = yl; } else { R.loh[r] = yh; R.lol[r] = yl; }
+                        const ff lo = ff_make(R.loh[r], R.lol[r]), hi = ff_make(R.hih[r], R.hil[r]);
+                        // root of the frozen-active-set quadratic a d^2 + b d + c = 0,
+                        // b = sum u x_new + tau Q y >= 0
+                        const float bq = fmaf(aQ, yh, F + ws.hi);
+                        const float cq = F * yh;
+                        const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
+                        const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
+                        ff yn = ff_add_f(ff_make(yh, yl), delta);
+                        // the frozen model may stand in for an evaluation at the new
+                        // y only when its own rounding error (cn A) is as small as the
+                        // final tolerance; far from the root evaluate again
+                        bool model = cn * Ab <= 2e-8f * ws.hi;
+                        if (!(ff_gt(yn, lo) && ff_gt(hi, yn))) {      // rounding left the bracket
+                            yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
+                            model = false;
+                        }
+                        if (yn.hi == yh && yn.lo == yl) {
+                            fin = true;                                // no representable progress
+                        } else {
+                            if (model) {
+                                R.ymh[r] = yh;
+                                R.yml[r] = yl;
+                                R.Cm[r] = C;
+                                R.Qm[r] = Q;
+                                R.st[r] = kRowCheck;
+                            }
+                            R.yh[r] = yn.hi;
+                            R.yl[r] = yn.lo;
+                            pending = true;
+                        }
+                    }
+                    if (fin) {
+                        R.Cf[r] = (double)C;
+                        R.st[r] = kRowDone;
                     }
                 }
             }
-            if (!__syncthreads_or(more)) break;
+            if (!__syncthreads_or(pending)) break;
         }
 
         // ---- utilities of the rows ----
         if (tid < nr) {
-            bf.t[hd.ra + tid] = R.s0[tid] - (double)R.Clast[tid];
+            bf.t[hd.ra + tid] = R.s0[tid] - R.Cf[tid];
             evals += R.nev[tid];
         }
 
@@ -503,8 +524,8 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
             RowRegs Rg;
             Rg.b = mk.rp[row];
             Rg.e = mk.rp[row + 1];
-            row_mixed_core<32, true>(mk, (const float*)mk.uv, Xin, Xout, Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc, row,
-                                     true, dxf, capped, evals, Rg);
+            row_mixed_core<32, true>(mk, (const float*)mk.uv, Xin, Xout, Xb, bf.pff, bf.pff, acc_s, bf.acc, bf.t, rc,
+                                     row, true, dxf, capped, evals, Rg);
         }
     }
 

@@ -76,8 +76,11 @@ def test_arrow_debreu_backward_matches_oracle(solver):
                               max_outer=400)
     gu_o, mu, info = A.ad_backward(mk.row_ptr, mk.col, mk.val, ad["x"], ad["p"], ad["t"], r)
     gu = host(gu)
-    assert np.array_equal(gu != 0, gu_o != 0)
-    assert np.max(np.abs(gu - gu_o)) <= 1e-4 * np.max(np.abs(gu_o))
+    scale = np.max(np.abs(gu_o))
+    # same tight graph: edge flows that vanish exactly in the oracle's tree
+    # solve come out of conjugate gradients at rounding level
+    assert np.array_equal(np.abs(gu) > 1e-9 * scale, np.abs(gu_o) > 1e-9 * scale)
+    assert np.max(np.abs(gu - gu_o)) <= 1e-4 * scale
 
 
 def test_batched_backward_matches_per_market_oracle(solver):
