@@ -145,6 +145,14 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
     float q2 = __fdiv_rn(r.hi, b.hi);
     return quick_two_sum(q1, q2);
 }
+// a / b from approximate reciprocals (a few ulp) and one exact correction:
+// accurate to about eps^2 like ff_div, without IEEE divisions
+__device__ __forceinline__ ff ff_div_fast(ff a, ff b) {
+    const float rb = __fdividef(1.0f, b.hi);
+    const float q1 = a.hi * rb;
+    const ff r = ff_sub(a, ff_mul_f(b, q1));
+    return quick_two_sum(q1, r.hi * rb);
+}
 // sqrt with one Newton correction: y + (a - y^2) / (2y)
 __device__ __forceinline__ ff ff_sqrt(ff a) {
     if (!(a.hi > 0.0f)) return ff_make(0.0f, 0.0f);
@@ -182,6 +190,18 @@ __device__ __forceinline__ float sr_add(float a, float b, unsigned r) {
     if (e == 0.0f || s == 0.0f) return s;
     const int sb = __float_as_int(s);
     const float nb = __int_as_float(((e > 0.0f) == (s > 0.0f)) ? sb + 1 : sb - 1);   // neighbour towards e
+    return (float)(r & 0xffffu) * (1.0f / 65536.0f) * fabsf(nb - s) < fabsf(e) ? nb : s;
+}
+
+// The same with Fast2Sum for the residual: exact when |a| >= |b| (a small
+// change to a stored value, the case that needs stochastic rounding); else
+// the result is still within one ulp of a + b.
+__device__ __forceinline__ float sr_add_fast(float a, float b, unsigned r) {
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    if (e == 0.0f || s == 0.0f) return s;
+    const int sb = __float_as_int(s);
+    const float nb = __int_as_float(((e > 0.0f) == (s > 0.0f)) ? sb + 1 : sb - 1);
     return (float)(r & 0xffffu) * (1.0f / 65536.0f) * fabsf(nb - s) < fabsf(e) ? nb : s;
 }
 

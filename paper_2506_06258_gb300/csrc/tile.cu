@@ -102,9 +102,7 @@ __device__ __forceinline__ void shared_add_f32(float* p, float v) {
 
 // thread 0: start the copies of tile t into a stage
 __device__ void tile_issue(const DevMarket& mk, const float* Xin, const float* Xb, const double* tprev, bool fold,
-                           int t, unsigned char* st, unsigned long long* bar, TileHdr* hd) {
-    const int2 rr = mk.tile_rows[t];
-    const longlong2 ee = mk.tile_ent[t];
+                           int2 rr, longlong2 ee, unsigned char* st, unsigned long long* bar, TileHdr* hd) {
     const long long A = ee.x & ~3LL;
     const unsigned vb = (unsigned)(((ee.y - A) + 3) & ~3LL) * 4u;        // <= kTileCap * 4
     const int ra2 = rr.x & ~1;
@@ -203,12 +201,29 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
     bool timed_out = false;
     int s = 0;
     int t = blockIdx.x;
-    if (tid == 0 && t < mk.ntiles) tile_issue(mk, Xin, Xb, bf.t, rc.fold, t, stages, &bar[0], &hdr[0]);
+    // thread 0 keeps the descriptor of the next tile in registers, loaded one
+    // tile ahead, so issuing a tile's copies never waits on memory
+    int2 nrr = make_int2(0, 0);
+    longlong2 nee;
+    nee.x = nee.y = 0;
+    if (tid == 0 && t < mk.ntiles) {
+        tile_issue(mk, Xin, Xb, bf.t, rc.fold, mk.tile_rows[t], mk.tile_ent[t], stages, &bar[0], &hdr[0]);
+        if (t + (int)gridDim.x < mk.ntiles) {
+            nrr = mk.tile_rows[t + gridDim.x];
+            nee = mk.tile_ent[t + gridDim.x];
+        }
+    }
 
     for (; t < mk.ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        if (tid == 0 && tn < mk.ntiles)
-            tile_issue(mk, Xin, Xb, bf.t, rc.fold, tn, stages + (size_t)(s ^ 1) * kStageBytes, &bar[s ^ 1], &hdr[s ^ 1]);
+        if (tid == 0 && tn < mk.ntiles) {
+            tile_issue(mk, Xin, Xb, bf.t, rc.fold, nrr, nee, stages + (size_t)(s ^ 1) * kStageBytes, &bar[s ^ 1],
+                       &hdr[s ^ 1]);
+            if (tn + (int)gridDim.x < mk.ntiles) {
+                nrr = mk.tile_rows[tn + gridDim.x];
+                nee = mk.tile_ent[tn + gridDim.x];
+            }
+        }
         const bool ok = mbar_wait(&bar[s], s ? par1 : par0);
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (s) par1 ^= 1u; else par0 ^= 1u;
@@ -228,12 +243,46 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
         const int ro = hd.ra & 1;
         const int L0 = (int)(hd.ea - A0), L1 = (int)(hd.eb - A0);
 
+        // ---- own entries: local positions Lb .. Lb + kTileE - 1; prices
+        // are gathered first so that their latency overlaps the row setup ----
+        const int Lb = tid * kTileE;
+        float u[kTileE], x[kTileE], ph[kTileE], pl[kTileE], td[kTileE];
+        int lr[kTileE], jj[kTileE];
+        unsigned actm = 0u;           // bit k: entry k active (tau d < x) at the last evaluation
+        {
+            const float4* u4 = (const float4*)(su + Lb);
+            const float4* x4 = (const float4*)(sx + Lb);
+            const int4* j4 = (const int4*)(sj + Lb);
+#pragma unroll
+            for (int q = 0; q < kTileE / 4; q++) {
+                const float4 a = u4[q], c = x4[q];
+                const int4 g = j4[q];
+                u[4 * q] = a.x; u[4 * q + 1] = a.y; u[4 * q + 2] = a.z; u[4 * q + 3] = a.w;
+                x[4 * q] = c.x; x[4 * q + 1] = c.y; x[4 * q + 2] = c.z; x[4 * q + 3] = c.w;
+                jj[4 * q] = g.x; jj[4 * q + 1] = g.y; jj[4 * q + 2] = g.z; jj[4 * q + 3] = g.w;
+            }
+#pragma unroll
+            for (int k = 0; k < kTileE; k++) {
+                const int L = Lb + k;
+                td[k] = 0.0f;
+                if (L < L0 || L >= L1) {
+                    lr[k] = -1;
+                    u[k] = 0.0f; x[k] = 0.0f; ph[k] = 0.0f; pl[k] = 0.0f;
+                } else {
+                    lr[k] = 0;
+                    const float2 p = __ldg(bf.pff + jj[k]);
+                    ph[k] = p.x;
+                    pl[k] = p.y;
+                }
+            }
+        }
+
         // ---- rows: offsets and the start y_0 = w / t_prev ----
         if (tid <= nr) R.off[tid] = (int)(srp[ro + tid] - A0);
         if (tid < nr) {
             const double tp = stp[ro + tid];
             ff y0 = ff_make(1.0f, 0.0f);
-            if (tp > 0.0 && tp < 1e300) y0 = ff_div(ff_from_double(sw[ro + tid]), ff_from_double(tp));
+            if (tp > 0.0 && tp < 1e300) y0 = ff_div_fast(ff_from_double(sw[ro + tid]), ff_from_double(tp));
             if (!(y0.hi > 0.0f) || !isfinite(y0.hi)) y0 = ff_make(1.0f, 0.0f);
             R.yh[tid] = y0.hi;
             R.yl[tid] = y0.lo;
@@ -252,23 +301,8 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
         }
         __syncthreads();
 
-        // ---- own entries: local positions Lb .. Lb + kTileE - 1 ----
-        const int Lb = tid * kTileE;
-        float u[kTileE], x[kTileE], ph[kTileE], pl[kTileE], td[kTileE];
-        int lr[kTileE], jj[kTileE];
-        unsigned actm = 0u;           // bit k: entry k active (tau d < x) at the last evaluation
+        // ---- row of each own entry ----
         {
-            const float4* u4 = (const float4*)(su + Lb);
-            const float4* x4 = (const float4*)(sx + Lb);
-            const int4* j4 = (const int4*)(sj + Lb);
-#pragma unroll
-            for (int q = 0; q < kTileE / 4; q++) {
-                const float4 a = u4[q], c = x4[q];
-                const int4 g = j4[q];
-                u[4 * q] = a.x; u[4 * q + 1] = a.y; u[4 * q + 2] = a.z; u[4 * q + 3] = a.w;
-                x[4 * q] = c.x; x[4 * q + 1] = c.y; x[4 * q + 2] = c.z; x[4 * q + 3] = c.w;
-                jj[4 * q] = g.x; jj[4 * q + 1] = g.y; jj[4 * q + 2] = g.z; jj[4 * q + 3] = g.w;
-            }
             int r = 0;
             const int Lf = max(Lb, L0);
             if (Lf < L1) {
@@ -281,18 +315,10 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
             }
 #pragma unroll
             for (int k = 0; k < kTileE; k++) {
+                if (lr[k] < 0) continue;
                 const int L = Lb + k;
-                td[k] = 0.0f;
-                if (L < L0 || L >= L1) {
-                    lr[k] = -1;
-                    u[k] = 0.0f; x[k] = 0.0f; ph[k] = 0.0f; pl[k] = 0.0f;
-                } else {
-                    while (R.off[r + 1] <= L) r++;
-                    lr[k] = r;
-                    const float2 p = __ldg(bf.pff + jj[k]);
-                    ph[k] = p.x;
-                    pl[k] = p.y;
-                }
+                while (R.off[r + 1] <= L) r++;
+                lr[k] = r;
             }
         }
 
@@ -383,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
                     R.Q[r] = 0.0f;
                     R.nev[r] += 1;
                     const ff s0 = ff_from_double(R.s0[r]);
-                    const ff ws = ff_div(ff_from_double(sw[ro + r]), ff_make(yh, yl));     // w / y
+                    const ff ws = ff_div_fast(ff_from_double(sw[ro + r]), ff_make(yh, yl));     // w / y
                     const ff D = ff_sub(s0, ws);
                     const float F = (D.hi - C) + D.lo;
                     // rounding bound of F: per-thread runs of kTileE terms, a warp
@@ -407,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
                         const float bq = fmaf(aQ, yh, F + ws.hi);
                         const float cq = F * yh;
                         const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
-                        const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
+                        const float delta = __fdividef(-2.0f * cq, bq + sqrtf(fmaxf(disc, 0.0f)));
                         ff yn = ff_add_f(ff_make(yh, yl), delta);
                         // the frozen model may stand in for an evaluation at the new
                         // y only when its own rounding error (cn A) is as small as the
@@ -468,13 +494,13 @@ __global__ void __launch_bounds__(kThreads, 2) tile_kernel(DevMarket mk, const v
                 rs ^= rs << 5;
                 if (lr[k] < 0) continue;
                 const unsigned rb = rs;
-                const float xn = td[k] < x[k] ? sr_add(x[k], -td[k], rb) : 0.0f;
+                const float xn = td[k] < x[k] ? sr_add_fast(x[k], -td[k], rb) : 0.0f;
                 xo[k] = xn;
                 const float dd = xn - x[k];
                 dxf = fmaf(dd, dd, dxf);
                 if (rc.fold) {
                     const float xb = xbo[k];
-                    xbo[k] = (fw == 1.0f) ? x[k] : sr_add(xb, fw * (x[k] - xb), rb >> 16);
+                    xbo[k] = (fw == 1.0f) ? x[k] : sr_add_fast(xb, fw * (x[k] - xb), rb >> 16);
                 }
                 acc_add_fixed(acc_s, bf.acc, hot, jj[k], xn);
             }
