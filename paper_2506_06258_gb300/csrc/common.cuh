@@ -30,12 +30,7 @@ constexpr int kWarps = 8;                               // warps per block of th
 constexpr int kThreads = kWarps * 32;
 constexpr int kMaxBuckets = 8;
 constexpr int kSlots = 4;                               // entries per lane held in registers
-// MIXED tile kernel: whole rows in CSR order, kTileE consecutive entries per thread
-constexpr int kTileE = 8;
-constexpr int kTileCap = kThreads * kTileE;             // entries per tile (from the 4-aligned start)
-constexpr int kTileRows = 128;                          // rows per tile
-constexpr int kTileHotMax = 3072;                       // hot goods staged in shared memory
-constexpr int kPadEntries = 16;                         // slack after nnz arrays read by bulk copies
+constexpr int kPadEntries = 16;                         // slack after the nnz arrays
 
 // ---------------------------------------------------------------------------
 // iteration control block (device resident; one per solve)
@@ -314,9 +309,6 @@ struct DevMarket {
     int hot;               // goods [0, hot) accumulate in shared memory
     int nprox;             // persistent grid of the row kernel (blocks)
     int mixed;             // value type of uv: 1 float, 0 double
-    int ntiles;            // MIXED: CSR tiles of whole rows (rows longer than a tile are in buckets)
-    const int2* tile_rows;        // rows [x, y) of each tile
-    const longlong2* tile_ent;    // entries [x, y) of each tile
 };
 
 struct IterBufs {
@@ -336,10 +328,6 @@ struct IterBufs {
 };
 
 int prox_blocks(bool mixed, int hot);  // persistent grid of the row kernel (occupancy based)
-int tile_blocks(int hot);               // persistent grid of the MIXED tile kernel (0: does not fit)
-int sm_count();
-void launch_tile(const DevMarket& mk, const IterBufs& b, Ctl* ctl, const void* x_in, void* x_out, int fixed,
-                 cudaStream_t s);
 int max_prox_blocks();                  // upper bound over all configurations
 void launch_price(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
 void launch_prox(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);

@@ -155,24 +155,6 @@ __global__ void max_scaled_t_kernel(int n, const long long* __restrict__ rp, con
     }
 }
 
-// t_i = u_i^T x_i (FP32 entries, FP64 sum), one warp per row
-__global__ void row_dot_f32_kernel(int n, const long long* __restrict__ rp, const float* __restrict__ uv,
-                                   const float* __restrict__ x, double* __restrict__ t) {
-    const int lane = threadIdx.x & 31;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = gw; i < n; i += nw) {
-        double a = 0.0;
-        for (long long q = rp[i] + lane; q < rp[i + 1]; q += 32) a = fma((double)uv[q], (double)x[q], a);
-        a = warp_sum_d(a);
-        if (lane == 0) t[i] = a;
-    }
-}
-
-void k_row_dot_f32(int n, const long long* rp, const float* uv, const float* x, double* t, cudaStream_t s) {
-    row_dot_f32_kernel<<<grid_for((long long)n * 32), 256, 0, s>>>(n, rp, uv, x, t);
-}
-
 void k_max_scaled_t(int n, const long long* rp, const float* uv, const double* t, double* out, cudaStream_t s) {
     max_scaled_t_kernel<<<grid_for((long long)n * 32), 256, 0, s>>>(n, rp, uv, t, out);
 }

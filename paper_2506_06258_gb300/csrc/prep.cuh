@@ -18,7 +18,6 @@ void k_fill(double* a, long long n, double v, cudaStream_t s);
 void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, cudaStream_t s);
 void k_scatter_goods(int m, const int* rank, const double* src, double* dst_int, cudaStream_t s);
 void k_util_out(int n, const double* t, const double* rowmax, double* out, cudaStream_t s);
-void k_row_dot_f32(int n, const long long* rp, const float* uv, const float* x, double* t, cudaStream_t s);
 void k_max_scaled_t(int n, const long long* rp, const float* uv, const double* t, double* out, cudaStream_t s);
 void k_convert(long long n, const void* src, bool src_f32, void* dst, bool dst_f32, cudaStream_t s);
 int dist_blocks();

@@ -337,7 +337,7 @@ static void set_smem_attr() {
     cudaFuncSetAttribute(prox_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-int sm_count() {
+static int sm_count() {
     static int sm = 0;
     if (!sm) {
         int dev = 0;
@@ -373,7 +373,7 @@ void launch_price(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, 
 }
 void launch_prox(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s) {
     set_smem_attr();
-    if (mixed) launch_tile(mk, b, ctl, nullptr, nullptr, 0, s);
+    if (mixed) prox_kernel<true><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, nullptr, nullptr, b, ctl, 0);
     else prox_kernel<false><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, nullptr, nullptr, b, ctl, 0);
 }
 void launch_dual(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s) {
@@ -444,7 +444,7 @@ void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* 
     b.pc = (double*)(acc + 2 * (size_t)mk.m);
     p_to_ff_kernel<<<vec_blocks(mk.m), 256, 0, s>>>(mk.m, p, b.pff, b.pc);
     ctl_fixed_kernel<<<1, 1, 0, s>>>(ctl, tau, 64);
-    if (mixed) launch_tile(mk, b, ctl, x_in, x_out, 1, s);
+    if (mixed) prox_kernel<true><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
     else prox_kernel<false><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
     cols_out_kernel<<<vec_blocks(mk.m), 256, 0, s>>>(mk.m, mixed, acc, c_out);
 }

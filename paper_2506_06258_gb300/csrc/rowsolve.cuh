@@ -138,7 +138,6 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
     const long long e = R.e;
     const float tau = rc.tau_hi;
     const double wd = valid ? mk.w[row] : 1.0;
-    const float wf = (float)wd;
     const int span = G * kSlots;
     const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
 
@@ -173,64 +172,69 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             }
         }
     };
+    // activity of the entries (tau d < x), one bit per entry of this lane
+    // (register rows: kSlots bits; chunked rows: kSlots bits per chunk, the
+    // first 64 / kSlots chunks; longer rows are always evaluated in full)
+    auto bit = [&](int c, int k) -> unsigned long long { return 1ull << ((c * kSlots + k) & 63); };
+    const bool track = nch * kSlots <= 64;
     // at (yh, yl): C = sum u min(tau d, x), A = sum u |min(tau d, x)|,
-    // Q = sum_active u^2 (active: tau d < x), and tau d of every entry
-    auto eval_chunk = [&](float yh, float yl, float& C, float& A, float& Q) {
+    // Q = sum_active u^2, the activity bits; with S: also s0 = u^T x^k
+    auto eval_chunk = [&](int c, float yh, float yl, float& C, float& A, float& Q, unsigned long long& act, bool S,
+                          ff& s0) {
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
             const float u = ru[k];
+            if (S) s0 = ff_add(s0, two_prod(u, rx[k]));
             const float d = fmaf(-u, yl, fmaf(-u, yh, rph[k]) + rpl[k]);
             const float td = tau * d;
             rtd[k] = td;
             const float cr = fminf(td, rx[k]);
             C = fmaf(u, cr, C);
             A = fmaf(u, fabsf(cr), A);
-            if (td < rx[k]) Q = fmaf(u, u, Q);
+            if (td < rx[k] && rj[k] >= 0) {
+                Q = fmaf(u, u, Q);
+                act |= bit(c, k);
+            }
         }
     };
 
-    // ---- s0 = u^T x^k in float-float; starting point y_0 = w / s0 ----
-    ff s0 = ff_make(0.0f, 0.0f);
-    for (int c = 0; c < nch; c++) {
-        if (LONG) load_chunk(c);
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) s0 = ff_add(s0, two_prod(ru[k], rx[k]));
-    }
-    if (!LONG) gather_p();
-    s0 = group_sum<G>(s0);
+    // ---- start y_0 = w / t of the previous pass (any y > 0 is a valid start) ----
     const ff wff = ff_from_double(wd);
-    float yh = (s0.hi > 0.0f) ? wf / s0.hi : 0.0f;
-    const bool need = !(yh > 0.0f) || !isfinite(yh);
-    if (__any_sync(0xffffffffu, need)) {
-        // x^k = 0 on this row: at y = max_j p_j / u_j every entry has d <= 0
-        float pmax_u = 0.0f;
-        for (int c = 0; c < nch; c++) {
-            if (LONG) { load_chunk(c); gather_p(); }
-#pragma unroll
-            for (int k = 0; k < kSlots; k++)
-                if (rj[k] >= 0) pmax_u = fmaxf(pmax_u, rph[k] / ru[k]);
+    float yh = 1.0f, yl = 0.0f;
+    if (valid) {
+        const double tp = t_out[row];
+        if (tp > 0.0 && tp < 1e300) {
+            const ff y0 = ff_div(wff, ff_from_double(tp));
+            if (y0.hi > 0.0f && isfinite(y0.hi)) { yh = y0.hi; yl = y0.lo; }
         }
-        for (int o = G / 2; o > 0; o >>= 1) pmax_u = fmaxf(pmax_u, __shfl_xor_sync(0xffffffffu, pmax_u, o));
-        if (need) yh = pmax_u > 0.0f ? pmax_u : 1.0f;
     }
+    // ---- first sweep: s0 and the evaluation at y_0 ----
+    ff s0 = ff_make(0.0f, 0.0f);
+    float C = 0.0f, A = 0.0f, Q = 0.0f;
+    unsigned long long act = 0ull;
+    if (!LONG) gather_p();
+    for (int c = 0; c < nch; c++) {
+        if (LONG) { load_chunk(c); gather_p(); }
+        eval_chunk(c, yh, yl, C, A, Q, act, true, s0);
+    }
+    s0 = group_sum<G>(s0);
+    C = group_sum<G>(C);
+    A = group_sum<G>(A);
+    Q = group_sum<G>(Q);
     // rounding bound of C: a lane adds nch*kSlots terms, then log2(G) levels
     const float cnoise = 1.2e-7f * (sqrtf((float)(nch * kSlots)) + 3.0f);
-    float yl = 0.0f, Clast = 0.0f;
     ff lo = ff_make(0.0f, 0.0f), hi = ff_make(INFINITY, 0.0f);   // bracket, in float-float
+    float Cf = 0.0f;
     bool done = !valid;
     int steps = 0, nev = 0;
+    // every lane of a group holds the group's identical sums, so the lanes of a
+    // row take identical decisions; rows of one warp may differ (any-loop)
     while (__any_sync(0xffffffffu, !done)) {
-        float C = 0.0f, A = 0.0f, Q = 0.0f;
-        for (int c = 0; c < nch; c++) {
-            if (LONG) { load_chunk(c); gather_p(); }
-            eval_chunk(yh, yl, C, A, Q);
-        }
-        C = group_sum<G>(C);
-        A = group_sum<G>(A);
-        Q = group_sum<G>(Q);
+        bool check = false;
+        float Cm = 0.0f, aQm = 0.0f;
+        ff ym = ff_make(yh, yl);
         if (!done) {
             nev++;
-            Clast = C;
             const ff ws = ff_div(wff, ff_make(yh, yl));    // w / y
             const ff D = ff_sub(s0, ws);
             const float F = (D.hi - C) + D.lo;
@@ -240,7 +244,8 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             const float floor = fmaf(cnoise, A, fmaf(3e-14f, aQ * yh, 2e-8f * ws.hi));
             if (fabsf(F) <= floor || ++steps >= rc.cap) {
                 done = true;
-                if (steps >= rc.cap && tl == 0 && valid) capped++;
+                Cf = C;
+                if (steps >= rc.cap && fabsf(F) > floor && tl == 0 && valid) capped++;
             } else {
                 if (F > 0.0f) hi = ff_make(yh, yl); else lo = ff_make(yh, yl);
                 // root of the frozen-active-set quadratic a d^2 + b d + c = 0,
@@ -250,32 +255,83 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
                 const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
                 const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
                 ff yn = ff_add_f(ff_make(yh, yl), delta);
-                if (!(ff_gt(yn, lo) && ff_gt(hi, yn)))       // rounding left the bracket
+                // the frozen model may replace an evaluation at the new y when
+                // its own rounding error is as small as the final tolerance
+                check = track && cnoise * A <= 2e-8f * ws.hi;
+                if (!(ff_gt(yn, lo) && ff_gt(hi, yn))) {     // rounding left the bracket
                     yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
-                if (yn.hi == yh && yn.lo == yl) done = true;   // no representable progress
-                yh = yn.hi;
-                yl = yn.lo;
+                    check = false;
+                }
+                if (yn.hi == yh && yn.lo == yl) {
+                    done = true;                              // no representable progress
+                    Cf = C;
+                } else {
+                    Cm = C;
+                    aQm = aQ;
+                    yh = yn.hi;
+                    yl = yn.lo;
+                }
             }
         }
+        // rows that took a model step: does any entry change activity at y?
+        bool chg = false;
+        const bool anycheck = __any_sync(0xffffffffu, check);
+        if (anycheck) {
+            for (int c = 0; c < nch; c++) {
+                if (LONG) { load_chunk(c); gather_p(); }
+#pragma unroll
+                for (int k = 0; k < kSlots; k++) {
+                    const float u = ru[k];
+                    const float td = tau * fmaf(-u, yl, fmaf(-u, yh, rph[k]) + rpl[k]);
+                    if (check) {
+                        rtd[k] = td;
+                        const bool a = td < rx[k] && rj[k] >= 0;
+                        chg |= a != ((act & bit(c, k)) != 0ull);
+                    }
+                }
+            }
+            chg = group_any<G>(chg);
+            if (check && !chg) {
+                done = true;
+                const float dy = (yh - ym.hi) + (yl - ym.lo);
+                Cf = Cm - aQm * dy;
+            }
+        }
+        // evaluation at the current y for rows still open
+        if (__any_sync(0xffffffffu, !done)) {
+            C = A = Q = 0.0f;
+            unsigned long long an = 0ull;
+            ff dummy = ff_make(0.0f, 0.0f);
+            for (int c = 0; c < nch; c++) {
+                if (LONG) { load_chunk(c); gather_p(); }
+                if (!done) eval_chunk(c, yh, yl, C, A, Q, an, false, dummy);
+            }
+            C = group_sum<G>(C);
+            A = group_sum<G>(A);
+            Q = group_sum<G>(Q);
+            if (!done) act = an;
+        }
     }
-    if (valid && tl == 0) evals += nev;
+    if (valid && tl == 0) {
+        t_out[row] = ((double)s0.hi + (double)s0.lo) - (double)Cf;
+        evals += nev;
+    }
 
-    // ---- new iterate (last evaluation), average fold, column sums ----
+    // ---- new iterate (at the final y), average fold, column sums ----
     const float fw = rc.fold_w;
     for (int c = 0; c < nch; c++) {
         if (LONG) {
             load_chunk(c);
             gather_p();
-            float C = 0.0f, A = 0.0f, Q = 0.0f;
-            eval_chunk(yh, yl, C, A, Q);
         }
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
             if (rj[k] < 0) continue;
             const long long idx = b + (long long)c * span + k * G + tl;
+            const float td = LONG ? tau * fmaf(-ru[k], yl, fmaf(-ru[k], yh, rph[k]) + rpl[k]) : rtd[k];
             const unsigned rb = sr_bits(idx, rc.seed);
             // x^{k+1} = [x^k - tau d]_+, stochastically rounded
-            const float xn = rtd[k] < rx[k] ? sr_add(rx[k], -rtd[k], rb) : 0.0f;
+            const float xn = td < rx[k] ? sr_add(rx[k], -td, rb) : 0.0f;
             __stcs(Xout + idx, xn);
             const float d = xn - rx[k];
             dx2 = fmaf(d, d, dx2);
@@ -286,7 +342,6 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
         }
     }
-    if (valid && tl == 0) t_out[row] = ((double)s0.hi + (double)s0.lo) - (double)Clast;
 }
 
 // Convenience form (loads the row itself): used by the batched kernel.

@@ -195,54 +195,7 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     D.nb = 0;
     D.mixed = mixed ? 1 : 0;
     std::vector<int> row_order;
-    if (mixed) {
-        // CSR tiles of whole rows for the tile kernel: at most kTileCap entries
-        // counted from the 4-aligned start, at most kTileRows rows; rows that do
-        // not fit a tile on their own go to one warp-chunked bucket
-        P.tile_rows.clear();
-        P.tile_ent.clear();
-        auto close = [&](int ra, int rb) {
-            if (rb > ra) {
-                P.tile_rows.push_back(make_int2(ra, rb));
-                longlong2 e;
-                e.x = rph[ra];
-                e.y = rph[rb];
-                P.tile_ent.push_back(e);
-            }
-        };
-        int ra = 0;
-        for (int i = 0; i < n; i++) {
-            const long long d = rph[i + 1] - rph[i];
-            if (d > kTileCap - 3) {
-                close(ra, i);
-                row_order.push_back(i);
-                ra = i + 1;
-                continue;
-            }
-            if (i - ra + 1 > kTileRows || rph[i + 1] - (rph[ra] & ~3LL) > kTileCap) {
-                close(ra, i);
-                ra = i;
-            }
-        }
-        close(ra, n);
-        if (!row_order.empty()) {
-            Bucket B;
-            B.g = 32;
-            B.chunks = 1;
-            B.first = 0;
-            B.count = (long long)row_order.size();
-            D.buckets[D.nb++] = B;
-        }
-        const size_t nt = P.tile_rows.size();
-        CK(ensure(h->tiles, nt * (sizeof(int2) + sizeof(longlong2)) + 16));
-        longlong2* te = (longlong2*)h->tiles.p;
-        int2* tr = (int2*)(te + nt);
-        CK(cudaMemcpyAsync(te, P.tile_ent.data(), nt * sizeof(longlong2), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(tr, P.tile_rows.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, s));
-        D.ntiles = (int)nt;
-        D.tile_ent = te;
-        D.tile_rows = tr;
-    } else {
+    {
         // rows by degree bucket
         const int caps[4] = {4 * kSlots, 8 * kSlots, 16 * kSlots, 32 * kSlots};
         const int gs[4] = {4, 8, 16, 32};
@@ -295,23 +248,12 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     D.row_order = (const int*)h->row_order.p;
     // hot goods in shared memory: as many as fit, but flushing them (blocks x
     // hot atomics) must stay small against nnz
-    long long hot = std::min<long long>(m, mixed ? kTileHotMax : 8192);
-    long long lim = nnz / (8LL * (mixed ? std::max(tile_blocks((int)hot), 1) : prox_blocks(mixed, (int)hot)));
+    long long hot = std::min<long long>(m, mixed ? 4096 : 8192);
+    long long lim = nnz / (8LL * prox_blocks(mixed, (int)hot));
     if (hot > lim) hot = lim;
     if (hot < 0) hot = 0;
-    if (mixed) {
-        // two tile blocks per SM (double-buffered stages) unless the hot goods do not fit
-        while (hot > 0 && tile_blocks((int)hot) < 2 * sm_count()) hot /= 2;
-        D.hot = (int)hot;
-        D.nprox = tile_blocks(D.hot);
-        if (D.nprox < 1) {
-            note_error(cudaErrorInvalidConfiguration, "tile kernel does not fit on this device");
-            return PDHCG_ERR_CUDA;
-        }
-    } else {
-        D.hot = (int)hot;
-        D.nprox = prox_blocks(mixed, D.hot);
-    }
+    D.hot = (int)hot;
+    D.nprox = prox_blocks(mixed, D.hot);
     // ||K||_2 = sqrt(max_j deg_j) for the column-sum operator on supp U
     int maxdeg = P.deg_int[0];
     P.normK = std::sqrt((double)maxdeg);
@@ -918,21 +860,9 @@ pdhcg_status pdhcg_row_prox(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precis
     double* co = (double*)out_loc(h->o_p, c_out, P.m * sizeof(double), &err);
     CK(err);
     CK(cudaMemsetAsync(h->acc.p, 0, P.m * sizeof(unsigned long long), s));
-    // the tile kernel reads its input by 16-byte bulk copies: run it on the
-    // padded internal buffers
-    const void* xk = xi;
-    void* xw = xo;
-    if (mixed) {
-        CK(cudaMemcpyAsync(h->X1.p, xi, P.nnz * vb, cudaMemcpyDeviceToDevice, s));
-        xk = h->X1.p;
-        xw = h->Xr.p;
-        // warm start of the row solve: t = u^T x_in
-        k_row_dot_f32(P.n, (const long long*)P.dm.rp, (const float*)P.dm.uv, (const float*)xk, (double*)h->t.p, s);
-    }
-    launch_prox_fixed(mixed, P.dm, xk, xw, (const double*)h->p0i.p, tau, (unsigned long long*)h->acc.p,
+    launch_prox_fixed(mixed, P.dm, xi, xo, (const double*)h->p0i.p, tau, (unsigned long long*)h->acc.p,
                       (double*)h->t.p, (double*)h->c_cur.p, (double*)h->part.p, (Ctl*)h->ctl.p, s);
     CK(cudaGetLastError());
-    if (mixed) CK(cudaMemcpyAsync(xo, h->Xr.p, P.nnz * vb, cudaMemcpyDeviceToDevice, s));
     if (so) {
         if (mixed) k_max_scaled_t(P.n, (const long long*)P.dm.rp, (const float*)P.dm.uv, (const double*)h->t.p, so, s);
         else CK(cudaMemcpyAsync(so, h->t.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
