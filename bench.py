@@ -214,6 +214,141 @@ def run_reference(args, cfg, rank):
     print(json.dumps(line), flush=True)
 
 
+
+# ---------------------------------------------------------------------------
+# comparison studies (not the bench line): each prints one JSON line
+# ---------------------------------------------------------------------------
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _study_c2(sol, S):
+    """C2: n = 1e6 buyers, m = 1e4 goods, 100 goods per buyer, LogNormal(0,1)
+    utilities; FP64 and MIXED GPU solves to relative KKT 1e-6 on the same GPU."""
+    import torch
+    mk = S.config2(fp32=True)
+    rp, col, w = _dev(mk.row_ptr), _dev(mk.col), _dev(mk.w)
+    out = {"workload": "C2: n=1e6, m=1e4, 100 distinct uniform goods per buyer (nnz=1e8), LogNormal(0,1), "
+                       "w~U(0.5,1.5), tol 1e-6", "nnz": int(mk.nnz)}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        val = _dev(mk.val.astype(np.float64) if prec == "fp64" else mk.val.astype(np.float32))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = sol.fisher_solve(rp, col, val, w, mk.m, tol=1e-6, precision=prec, max_iter=100000, check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[prec] = o
+        out[prec] = {"status": int(o.status), "seconds": dt, "iters": int(o.info["iters"]),
+                     "kkt": o.info["kkt"], "iters_per_s": o.info["iters"] / max(o.info["solve_ms"] * 1e-3, 1e-9)}
+        del val
+    pf, pm = res["fp64"].p, res["mixed"].p
+    out["mixed_vs_fp64_price_rel_max"] = float(torch.max(torch.abs(pm - pf) / pf).item())
+    out["mixed_vs_fp64_util_rel_max"] = float(torch.max(torch.abs(res["mixed"].util - res["fp64"].util)
+                                                         / res["fp64"].util).item())
+    return out
+
+
+def _study_c5(sol, S):
+    """256 markets of the C5 law (n~UI[50,5000], m~UI[20,2000],
+    density~U(0.05,0.3)): one batched persistent launch to tolerance 1e-6 (120 s cap),
+    MIXED and FP64; the batched backward of sum p.r; a loop of single-market
+    solves on 16 markets."""
+    import torch
+    from paper_2506_06258_gb300 import capi
+    bt = S.config5(B=256)
+    N, M, NNZ = int(bt.row_off[-1]), int(bt.good_off[-1]), int(bt.nnz_off[-1])
+    out = {"workload": "256 markets of the C5 law, n~UI[50,5000], m~UI[20,2000], density~U(0.05,0.3), u~U(0,1), "
+                       "w~U(0.5,1.5), tol 1e-6", "markets": bt.B, "rows": N, "goods": M, "nnz": NNZ}
+    nnz_b = np.diff(bt.nnz_off)
+    for prec in ("mixed", "fp64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = sol.solve_batched(bt, tol=1e-6, precision=prec, check=False, time_limit_s=120.0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        its = np.array([i["iters"] for i in o.info])
+        st = np.array([i["status"] for i in o.info])
+        kk = np.array([i["kkt"] for i in o.info])
+        print(json.dumps({"study": "c5", "stage": prec, "seconds": dt}), flush=True)
+        out[prec] = {"seconds": dt, "solve_ms": o.info[0]["solve_ms"], "converged": int((st == 0).sum()),
+                     "status_counts": {str(k): int((st == k).sum()) for k in np.unique(st)},
+                     "max_kkt": float(kk.max()), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                     "algorithmic_GB_per_s": float((its * nnz_b).sum() * (24.0 if prec == "mixed" else 44.0)
+                                                   / (o.info[0]["solve_ms"] * 1e-3) / 1e9)}
+        if prec == "mixed":
+            p_mixed = o.p.clone()
+            if (st == 0).all():     # the derivative needs every market at its equilibrium
+                r = torch.from_numpy(np.random.default_rng(5).normal(size=M)).cuda()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                sol.backward(r, None, nnz=NNZ, n=N)
+                torch.cuda.synchronize()
+                out["mixed"]["backward_seconds"] = time.perf_counter() - t1
+        else:
+            out["mixed_vs_fp64_price_rel_max"] = float(torch.max(torch.abs(p_mixed - o.p) / o.p).item())
+    print(json.dumps({"study": "c5", "partial": True, **out}), flush=True)
+    # loop of single-market solves on the first 16 markets
+    t0 = time.perf_counter()
+    for b in range(16):
+        mk = bt.market(b)
+        sol.fisher_solve(_dev(mk.row_ptr), _dev(mk.col), _dev(mk.val.astype(np.float32)), _dev(mk.w), mk.m,
+                         tol=1e-6, precision="mixed", check=False)
+    torch.cuda.synchronize()
+    loop = time.perf_counter() - t0
+    out["single_solve_loop_16_markets_seconds"] = loop
+    out["single_solve_loop_extrapolated_seconds"] = loop * bt.B / 16
+    return out
+
+
+def _study_c4(sol, S):
+    """C4: Arrow-Debreu exchange economy n = m = 1e5, own good + 50 others,
+    u~U(0.1,1), w0 = 1, E = I; MIXED fixed point to a relative change < 1e-6
+    (inner tolerance 1e-7) and the derivative of sum r_j p_j w.r.t. u at it;
+    FP64 fixed point with inner tolerance 1e-8 for the price comparison (both
+    capped at 150 s).  Central differences of the derivative are checked on
+    small markets by the test suite."""
+    import torch
+    mk = S.config4(fp32=True)
+    r = np.random.default_rng(3).normal(size=mk.m)
+    rp, col, w0 = _dev(mk.row_ptr), _dev(mk.col), _dev(mk.w)
+    out = {"workload": "C4: Arrow-Debreu, n=m=1e5, own good + 50 distinct others (nnz=5.1e6), u~U(0.1,1), "
+                       "w0=1, E=I, outer tol 1e-6", "nnz": int(mk.nnz)}
+    res = {}
+    for prec, itol in (("mixed", 1e-7), ("fp64", 1e-8)):
+        val = _dev(mk.val.astype(np.float32) if prec == "mixed" else mk.val.astype(np.float64))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = sol.ad_solve(rp, col, val, w0, mk.m, outer_tol=1e-6, tol=itol, precision=prec, max_outer=100,
+                         check=False, time_limit_s=150.0)
+        torch.cuda.synchronize()
+        out[prec] = {"seconds": time.perf_counter() - t0, "status": int(o.status), "outer": int(o.info["outer"]),
+                     "inner_iters": int(o.info["iters"]), "kkt": o.info["kkt"]}
+        res[prec] = o.p.clone()
+        if prec == "mixed" and o.status == 0:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            sol.backward(_dev(r), None, nnz=mk.nnz, n=mk.n)
+            torch.cuda.synchronize()
+            out["mixed"]["backward_seconds"] = time.perf_counter() - t1
+    out["mixed_vs_fp64_price_rel_max"] = float(torch.max(torch.abs(res["mixed"] - res["fp64"]) / res["fp64"]).item())
+    return out
+
+
+def run_study(which):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2506_06258_gb300 import api, synth as S
+    torch.cuda.set_device(0)
+    sol = api.Solver()
+    fn = {"c2": _study_c2, "c4": _study_c4, "c5": _study_c5}[which]
+    out = fn(sol, S)
+    sol.close()
+    print(json.dumps({"study": which, **out}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -226,6 +361,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-tol", action="store_true", help="also run one full solve to tol 1e-6")
+    ap.add_argument("--study", choices=["c2", "c4", "c5"], default=None,
+                    help="instead of the bench line, run one comparison study and print its JSON line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -235,6 +372,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, cfg, rank)
+        return
+    if args.study:
+        run_study(args.study)
         return
 
     import torch
