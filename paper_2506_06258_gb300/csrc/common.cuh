@@ -140,22 +140,6 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
     float q2 = __fdiv_rn(r.hi, b.hi);
     return quick_two_sum(q1, q2);
 }
-// a / b from approximate reciprocals (a few ulp) and one exact correction:
-// accurate to about eps^2 like ff_div, without IEEE divisions
-__device__ __forceinline__ ff ff_div_fast(ff a, ff b) {
-    const float rb = __fdividef(1.0f, b.hi);
-    const float q1 = a.hi * rb;
-    const ff r = ff_sub(a, ff_mul_f(b, q1));
-    return quick_two_sum(q1, r.hi * rb);
-}
-// sqrt with one Newton correction: y + (a - y^2) / (2y)
-__device__ __forceinline__ ff ff_sqrt(ff a) {
-    if (!(a.hi > 0.0f)) return ff_make(0.0f, 0.0f);
-    float y = __fsqrt_rn(a.hi);
-    ff e = ff_sub(a, two_prod(y, y));
-    return quick_two_sum(y, __fdiv_rn(e.hi, __fmul_rn(2.0f, y)));
-}
-__device__ __forceinline__ bool ff_pos(ff a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
 // ---------------------------------------------------------------------------
 // stochastic rounding of FP32 iterates
 // ---------------------------------------------------------------------------
@@ -188,17 +172,6 @@ __device__ __forceinline__ float sr_add(float a, float b, unsigned r) {
     return (float)(r & 0xffffu) * (1.0f / 65536.0f) * fabsf(nb - s) < fabsf(e) ? nb : s;
 }
 
-// The same with Fast2Sum for the residual: exact when |a| >= |b| (a small
-// change to a stored value, the case that needs stochastic rounding); else
-// the result is still within one ulp of a + b.
-__device__ __forceinline__ float sr_add_fast(float a, float b, unsigned r) {
-    const float s = __fadd_rn(a, b);
-    const float e = __fsub_rn(b, __fsub_rn(s, a));
-    if (e == 0.0f || s == 0.0f) return s;
-    const int sb = __float_as_int(s);
-    const float nb = __int_as_float(((e > 0.0f) == (s > 0.0f)) ? sb + 1 : sb - 1);
-    return (float)(r & 0xffffu) * (1.0f / 65536.0f) * fabsf(nb - s) < fabsf(e) ? nb : s;
-}
 
 // a > b for normalised float-float values
 __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
@@ -235,10 +208,6 @@ __device__ __forceinline__ unsigned long long shared_cas_b64(unsigned long long*
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double d) { return (unsigned long long)__double_as_longlong(d); }
 
-// max of non-negative doubles through their bit patterns
-__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
-    if (v > 0.0) atomicMax(a, dbits(v));
-}
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v) {

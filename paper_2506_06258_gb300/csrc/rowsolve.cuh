@@ -7,8 +7,8 @@
 // positive root is a lower bound of s* (the frozen sum is a minorant that
 // touches at s), and iterating "active set -> root" climbs monotonically to
 // s*, ending when the active set no longer changes, at which point the root is
-// exact.  MIXED form: safeguarded Newton on y = w/s with cancellation-free
-// residuals (see row_mixed).
+// exact.  MIXED form: the same iteration written in y = w/s, on
+// cancellation-free residuals (see row_mixed_core).
 #pragma once
 #include "common.cuh"
 
@@ -17,17 +17,6 @@ namespace pdhcg {
 // ---------------------------------------------------------------------------
 // positive root of s^2 - A s - C = 0 (C >= 0), cancellation free
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float root32(float A, float C) {
-    float D = fmaf(A, A, 4.0f * C);
-    float sq = sqrtf(fmaxf(D, 0.0f));
-    return A >= 0.0f ? 0.5f * (A + sq) : (2.0f * C) / (sq - A);
-}
-__device__ __forceinline__ ff root_ff(ff A, ff C) {
-    ff D = ff_add(ff_mul(A, A), ff_mul_f(C, 4.0f));
-    ff sq = ff_sqrt(D);
-    if (A.hi >= 0.0f) return ff_mul_f(ff_add(A, sq), 0.5f);
-    return ff_div(ff_mul_f(C, 2.0f), ff_sub(sq, A));
-}
 __device__ __forceinline__ double root64(double A, double C) {
     double D = fma(A, A, 4.0 * C);
     double sq = sqrt(fmax(D, 0.0));
@@ -89,10 +78,13 @@ struct RowCtx {
 // min(tau d_j, x_j) is concave in y, so the frozen model lies below F and its
 // root is an upper bound of y*: after the first step the iterates decrease
 // monotonically to y* and stop once the active set no longer changes (the
-// same finite active-set iteration as the FP64 form, written in y).  Start
-// at y_0 = w / s0 (the paper's trial value); a bracket [lo, hi] on the sign of
-// F guards against rounding; stop when |F| is below the rounding bound of its
-// evaluation or y no longer moves.
+// same finite active-set iteration as the FP64 form, written in y).  Each row
+// starts from y_0 = w / t of the previous pass, so s0 and the evaluation at
+// y_0 share one sweep; after a frozen-model step whose own rounding error is
+// within the final tolerance, a sweep without reductions checks that no entry
+// changed activity, which makes the model exact at the new y.  A bracket
+// [lo, hi] on the sign of F guards against rounding; stop when |F| is below
+// the rounding bound of its evaluation or y no longer moves.
 // ---------------------------------------------------------------------------
 // Entries of one row held by one lane (register-resident rows).
 struct RowRegs {
