@@ -87,10 +87,13 @@ def test_two_by_two(solver, prec, tol, rtol, case):
     assert np.allclose(host(out.util), t, rtol=rtol)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 2e-7)])
 def test_single_good_buyers_and_long_rows(solver, prec, tol):
     """Half the buyers want one good each; a few buyers want 300-900 goods
-    (the chunked row path); the rest are ordinary."""
+    (the chunked row path); the rest are ordinary.  On this market the price
+    error is about 9x the relative KKT error even for the FP64 oracle (5.7e-6
+    at KKT 6.2e-7), so both precisions are solved below 1e-6 to test a 1e-5
+    price bound."""
     rng = np.random.default_rng(4)
     n, m = 600, 1000
     deg = np.where(np.arange(n) % 2 == 0, 1, rng.integers(2, 40, n))
