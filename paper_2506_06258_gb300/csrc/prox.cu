@@ -56,7 +56,7 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
                 rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
                 row_load<G>(mk, U, Xi, rn, vn, nx);
             }
-            row_mixed_core<G, false>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
+            row_mixed_core<G>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
                                      rc_row, vc, dxf, capped, evals, cr);
         }
     }
@@ -118,12 +118,8 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
                 bool valid = slot < bk.count;
                 int row = valid ? mk.row_order[bk.first + slot] : 0;
                 if (MIXED) {
-                    RowRegs R;
-                    R.b = valid ? mk.rp[row] : 0;
-                    R.e = valid ? mk.rp[row + 1] : 0;
-                    row_mixed_core<32, true>(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout,
-                                             (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf,
-                                             capped, evals, R);
+                    row_mixed_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff,
+                                   sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped, evals);
                 } else {
                     const double* U = (const double*)mk.uv;
                     double* Xo = (double*)Xout;

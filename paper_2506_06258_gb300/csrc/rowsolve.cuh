@@ -52,9 +52,9 @@ struct RowCtx {
 };
 
 // ---------------------------------------------------------------------------
-// MIXED row solve: G lanes per row, row data either in registers (LONG=false,
-// d <= G*kSlots) or streamed in chunks of 32*kSlots (LONG=true, G=32).
-// Every lane of the warp calls this together; `valid` marks real rows.
+// MIXED row solve: G lanes per row, row data in registers (d <= G*kSlots;
+// longer rows: row_mixed_long below).  Every lane of the warp calls this
+// together; `valid` marks real rows.
 //
 // Unknown y = w / s (the buyer's price of utility).  With d_j = p_j - u_j y the
 // row equation of Section 2.2 reads
@@ -119,7 +119,7 @@ __device__ __forceinline__ float2 price_ff(const float2* __restrict__ pff, const
     return j < hot ? sp[j] : __ldg(pff + j);
 }
 
-template <int G, bool LONG>
+template <int G>
 __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
                                float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
                                const float2* sp, unsigned long long* acc_s, unsigned long long* acc_g,
@@ -127,52 +127,29 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
                                int& capped, int& evals, RowRegs& R) {
     const int tl = (threadIdx.x & 31) & (G - 1);
     const long long b = R.b;
-    const long long e = R.e;
     const float tau = rc.tau_hi;
     const double wd = valid ? mk.w[row] : 1.0;
-    const int span = G * kSlots;
-    const int nch = LONG ? (int)((e - b + span - 1) / span) : 1;
 
     float rph[kSlots], rpl[kSlots], rtd[kSlots];
     float* ru = R.u;
     float* rx = R.x;
     int* rj = R.j;
 
-    auto load_chunk = [&](int c) {
 #pragma unroll
-        for (int k = 0; k < kSlots; k++) {
-            const long long idx = b + (long long)c * span + k * G + tl;
-            if (idx < e) {
-                rj[k] = __ldg(mk.cj + idx);
-                ru[k] = __ldg(U + idx);
-                rx[k] = Xin[idx];
-            } else {
-                rj[k] = -1; ru[k] = 0.0f; rx[k] = 0.0f;
-            }
+    for (int k = 0; k < kSlots; k++) {
+        if (rj[k] >= 0) {
+            const float2 p = price_ff(pff, sp, mk.hot, rj[k]);
+            rph[k] = p.x;
+            rpl[k] = p.y;
+        } else {
+            rph[k] = 0.0f;
+            rpl[k] = 0.0f;
         }
-    };
-    auto gather_p = [&]() {
-#pragma unroll
-        for (int k = 0; k < kSlots; k++) {
-            if (rj[k] >= 0) {
-                const float2 p = price_ff(pff, sp, mk.hot, rj[k]);
-                rph[k] = p.x;
-                rpl[k] = p.y;
-            } else {
-                rph[k] = 0.0f;
-                rpl[k] = 0.0f;
-            }
-        }
-    };
-    // activity of the entries (tau d < x), one bit per entry of this lane
-    // (register rows: kSlots bits; chunked rows: kSlots bits per chunk, the
-    // first 64 / kSlots chunks; longer rows are always evaluated in full)
-    auto bit = [&](int c, int k) -> unsigned long long { return 1ull << ((c * kSlots + k) & 63); };
-    const bool track = nch * kSlots <= 64;
+    }
     // at (yh, yl): C = sum u min(tau d, x), A = sum u |min(tau d, x)|,
-    // Q = sum_active u^2, the activity bits; with S: also s0 = u^T x^k
-    auto eval_chunk = [&](int c, float yh, float yl, float& C, float& A, float& Q, unsigned long long& act, bool S,
-                          ff& s0) {
+    // Q = sum_active u^2, the activity bits (tau d < x, one per entry of this
+    // lane); with S: also s0 = u^T x^k
+    auto eval = [&](float yh, float yl, float& C, float& A, float& Q, unsigned& act, bool S, ff& s0) {
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
             const float u = ru[k];
@@ -185,7 +162,7 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             A = fmaf(u, fabsf(cr), A);
             if (td < rx[k] && rj[k] >= 0) {
                 Q = fmaf(u, u, Q);
-                act |= bit(c, k);
+                act |= 1u << k;
             }
         }
     };
@@ -203,18 +180,14 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
     // ---- first sweep: s0 and the evaluation at y_0 ----
     ff s0 = ff_make(0.0f, 0.0f);
     float C = 0.0f, A = 0.0f, Q = 0.0f;
-    unsigned long long act = 0ull;
-    if (!LONG) gather_p();
-    for (int c = 0; c < nch; c++) {
-        if (LONG) { load_chunk(c); gather_p(); }
-        eval_chunk(c, yh, yl, C, A, Q, act, true, s0);
-    }
+    unsigned act = 0u;
+    eval(yh, yl, C, A, Q, act, true, s0);
     s0 = group_sum<G>(s0);
     C = group_sum<G>(C);
     A = group_sum<G>(A);
     Q = group_sum<G>(Q);
-    // rounding bound of C: a lane adds nch*kSlots terms, then log2(G) levels
-    const float cnoise = 1.2e-7f * (sqrtf((float)(nch * kSlots)) + 3.0f);
+    // rounding bound of C: a lane adds kSlots terms, then log2(G) levels
+    const float cnoise = 1.2e-7f * (sqrtf((float)kSlots) + 3.0f);
     ff lo = ff_make(0.0f, 0.0f), hi = ff_make(INFINITY, 0.0f);   // bracket, in float-float
     float Cf = 0.0f;
     bool done = !valid;
@@ -249,7 +222,7 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
                 ff yn = ff_add_f(ff_make(yh, yl), delta);
                 // the frozen model may replace an evaluation at the new y when
                 // its own rounding error is as small as the final tolerance
-                check = track && cnoise * A <= 2e-8f * ws.hi;
+                check = cnoise * A <= 2e-8f * ws.hi;
                 if (!(ff_gt(yn, lo) && ff_gt(hi, yn))) {     // rounding left the bracket
                     yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
                     check = false;
@@ -266,20 +239,16 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
             }
         }
         // rows that took a model step: does any entry change activity at y?
-        bool chg = false;
-        const bool anycheck = __any_sync(0xffffffffu, check);
-        if (anycheck) {
-            for (int c = 0; c < nch; c++) {
-                if (LONG) { load_chunk(c); gather_p(); }
+        if (__any_sync(0xffffffffu, check)) {
+            bool chg = false;
 #pragma unroll
-                for (int k = 0; k < kSlots; k++) {
-                    const float u = ru[k];
-                    const float td = tau * fmaf(-u, yl, fmaf(-u, yh, rph[k]) + rpl[k]);
-                    if (check) {
-                        rtd[k] = td;
-                        const bool a = td < rx[k] && rj[k] >= 0;
-                        chg |= a != ((act & bit(c, k)) != 0ull);
-                    }
+            for (int k = 0; k < kSlots; k++) {
+                const float u = ru[k];
+                const float td = tau * fmaf(-u, yl, fmaf(-u, yh, rph[k]) + rpl[k]);
+                if (check) {
+                    rtd[k] = td;
+                    const bool a = td < rx[k] && rj[k] >= 0;
+                    chg |= a != ((act >> k) & 1u);
                 }
             }
             chg = group_any<G>(chg);
@@ -292,12 +261,9 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
         // evaluation at the current y for rows still open
         if (__any_sync(0xffffffffu, !done)) {
             C = A = Q = 0.0f;
-            unsigned long long an = 0ull;
+            unsigned an = 0u;
             ff dummy = ff_make(0.0f, 0.0f);
-            for (int c = 0; c < nch; c++) {
-                if (LONG) { load_chunk(c); gather_p(); }
-                if (!done) eval_chunk(c, yh, yl, C, A, Q, an, false, dummy);
-            }
+            if (!done) eval(yh, yl, C, A, Q, an, false, dummy);
             C = group_sum<G>(C);
             A = group_sum<G>(A);
             Q = group_sum<G>(Q);
@@ -311,28 +277,262 @@ __device__ void row_mixed_core(const DevMarket& mk, const float* __restrict__ U,
 
     // ---- new iterate (at the final y), average fold, column sums ----
     const float fw = rc.fold_w;
-    for (int c = 0; c < nch; c++) {
-        if (LONG) {
-            load_chunk(c);
-            gather_p();
+#pragma unroll
+    for (int k = 0; k < kSlots; k++) {
+        if (rj[k] < 0) continue;
+        const long long idx = b + k * G + tl;
+        const float td = rtd[k];
+        const unsigned rb = sr_bits(idx, rc.seed);
+        // x^{k+1} = [x^k - tau d]_+, stochastically rounded
+        const float xn = td < rx[k] ? sr_add(rx[k], -td, rb) : 0.0f;
+        __stcs(Xout + idx, xn);
+        const float d = xn - rx[k];
+        dx2 = fmaf(d, d, dx2);
+        if (rc.fold) {
+            const float xb = Xb[idx];
+            Xb[idx] = (fw == 1.0f) ? rx[k] : sr_add(xb, fw * (rx[k] - xb), rb >> 16);
+        }
+        acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MIXED row solve for rows longer than 32*kSlots entries: one warp per row,
+// the row streamed in chunks of 32*kSlots entries and re-read (from L2) on
+// every sweep.  Iteration, stopping rule and rounding are those of
+// row_mixed_core, entry for entry; what differs is the number of sweeps:
+//  - x-bar is folded during the first sweep (the fold needs x^k only);
+//  - the first activity check (after a frozen-model step) writes x^{k+1}, its
+//    column sums and ||dx||^2 at the new y chunk by chunk behind the check.
+//    When no entry changes activity that y is final and no separate write
+//    sweep follows; at the first chunk that shows a change the check stops,
+//    the column-sum contributions of the chunks already written are
+//    subtracted again (exact: the sums are fixed-point integers), ||dx||^2 is
+//    restored, and the iteration continues without further speculation.
+// Every lane of the warp calls this with the same row.
+// ---------------------------------------------------------------------------
+__device__ inline void row_mixed_long(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
+                               float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
+                               const float2* sp, unsigned long long* acc_s, unsigned long long* acc_g,
+                               double* __restrict__ t_out, const RowCtx& rc, int row, bool valid, float& dx2,
+                               int& capped, int& evals) {
+    if (!valid) return;
+    const int lane = threadIdx.x & 31;
+    constexpr int span = 32 * kSlots;
+    const long long b = mk.rp[row];
+    const long long e = mk.rp[row + 1];
+    const int nch = (int)((e - b + span - 1) / span);
+    const float tau = rc.tau_hi;
+
+    float ru[kSlots], rx[kSlots], rph[kSlots], rpl[kSlots], rtd[kSlots];
+    int rj[kSlots];
+    auto load_chunk = [&](int c) {
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            const long long idx = b + (long long)c * span + k * 32 + lane;
+            if (idx < e) {
+                rj[k] = __ldg(mk.cj + idx);
+                ru[k] = __ldg(U + idx);
+                rx[k] = Xin[idx];
+            } else {
+                rj[k] = -1; ru[k] = 0.0f; rx[k] = 0.0f;
+            }
         }
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
-            if (rj[k] < 0) continue;
-            const long long idx = b + (long long)c * span + k * G + tl;
-            const float td = LONG ? tau * fmaf(-ru[k], yl, fmaf(-ru[k], yh, rph[k]) + rpl[k]) : rtd[k];
-            const unsigned rb = sr_bits(idx, rc.seed);
-            // x^{k+1} = [x^k - tau d]_+, stochastically rounded
-            const float xn = td < rx[k] ? sr_add(rx[k], -td, rb) : 0.0f;
-            __stcs(Xout + idx, xn);
-            const float d = xn - rx[k];
-            dx2 = fmaf(d, d, dx2);
-            if (rc.fold) {
-                const float xb = Xb[idx];
-                Xb[idx] = (fw == 1.0f) ? rx[k] : sr_add(xb, fw * (rx[k] - xb), rb >> 16);
+            if (rj[k] >= 0) {
+                const float2 p = price_ff(pff, sp, mk.hot, rj[k]);
+                rph[k] = p.x;
+                rpl[k] = p.y;
+            } else {
+                rph[k] = 0.0f;
+                rpl[k] = 0.0f;
             }
-            acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
         }
+    };
+    auto td_at = [&](int k, float yh, float yl) -> float {
+        return tau * fmaf(-ru[k], yl, fmaf(-ru[k], yh, rph[k]) + rpl[k]);
+    };
+    // x^{k+1} of the loaded chunk from rtd: store, ||dx||^2, column sums; with
+    // undo, subtract the column-sum contributions written by the same call
+    auto write_chunk = [&](int c, bool undo) {
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            if (rj[k] < 0) continue;
+            const long long idx = b + (long long)c * span + k * 32 + lane;
+            const float td = rtd[k];
+            const float xn = td < rx[k] ? sr_add(rx[k], -td, sr_bits(idx, rc.seed)) : 0.0f;
+            if (!undo) {
+                __stcs(Xout + idx, xn);
+                const float d = xn - rx[k];
+                dx2 = fmaf(d, d, dx2);
+                acc_add_fixed(acc_s, acc_g, mk.hot, rj[k], xn);
+            } else if (xn > 0.0f) {
+                const unsigned long long v = 0ull - (unsigned long long)__float2ll_rn(xn * kFixScaleF);
+                if (rj[k] < mk.hot) shared_add_u64(&acc_s[rj[k]], v);
+                else atomicAdd(&acc_g[rj[k]], v);
+            }
+        }
+    };
+    auto undo_chunks = [&](int cw, float yh, float yl) {
+        for (int c = 0; c < cw; c++) {
+            load_chunk(c);
+#pragma unroll
+            for (int k = 0; k < kSlots; k++) rtd[k] = td_at(k, yh, yl);
+            write_chunk(c, true);
+        }
+    };
+    auto bit = [&](int c, int k) -> unsigned long long { return 1ull << ((c * kSlots + k) & 63); };
+    const bool track = nch * kSlots <= 64;
+
+    // ---- start y_0 = w / t of the previous pass ----
+    const ff wff = ff_from_double(mk.w[row]);
+    float yh = 1.0f, yl = 0.0f;
+    {
+        const double tp = t_out[row];
+        if (tp > 0.0 && tp < 1e300) {
+            const ff y0 = ff_div(wff, ff_from_double(tp));
+            if (y0.hi > 0.0f && isfinite(y0.hi)) { yh = y0.hi; yl = y0.lo; }
+        }
+    }
+    // ---- first sweep: s0, the evaluation at y_0, the x-bar fold ----
+    const float fw = rc.fold_w;
+    ff s0 = ff_make(0.0f, 0.0f);
+    float C = 0.0f, A = 0.0f, Q = 0.0f;
+    unsigned long long act = 0ull;
+    for (int c = 0; c < nch; c++) {
+        load_chunk(c);
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) {
+            const float u = ru[k];
+            s0 = ff_add(s0, two_prod(u, rx[k]));
+            const float td = td_at(k, yh, yl);
+            const float cr = fminf(td, rx[k]);
+            C = fmaf(u, cr, C);
+            A = fmaf(u, fabsf(cr), A);
+            if (td < rx[k] && rj[k] >= 0) {
+                Q = fmaf(u, u, Q);
+                act |= bit(c, k);
+            }
+            if (rc.fold && rj[k] >= 0) {
+                const long long idx = b + (long long)c * span + k * 32 + lane;
+                const float xb = Xb[idx];
+                Xb[idx] = (fw == 1.0f) ? rx[k] : sr_add(xb, fw * (rx[k] - xb), sr_bits(idx, rc.seed) >> 16);
+            }
+        }
+    }
+    s0 = group_sum<32>(s0);
+    C = group_sum<32>(C);
+    A = group_sum<32>(A);
+    Q = group_sum<32>(Q);
+    const float cnoise = 1.2e-7f * (sqrtf((float)(nch * kSlots)) + 3.0f);
+    ff lo = ff_make(0.0f, 0.0f), hi = ff_make(INFINITY, 0.0f);
+    float Cf = 0.0f;
+    int steps = 0, nev = 0;
+    bool spec = true;        // the next activity check may write x^{k+1} behind it
+    bool written = false;    // x^{k+1} written at the final y
+    while (true) {
+        nev++;
+        const ff ws = ff_div(wff, ff_make(yh, yl));
+        const ff D = ff_sub(s0, ws);
+        const float F = (D.hi - C) + D.lo;
+        const float aQ = tau * Q;
+        const float floor = fmaf(cnoise, A, fmaf(3e-14f, aQ * yh, 2e-8f * ws.hi));
+        if (fabsf(F) <= floor || ++steps >= rc.cap) {
+            Cf = C;
+            if (steps >= rc.cap && fabsf(F) > floor && lane == 0) capped++;
+            break;
+        }
+        if (F > 0.0f) hi = ff_make(yh, yl); else lo = ff_make(yh, yl);
+        const float bq = fmaf(aQ, yh, F + ws.hi);
+        const float cq = F * yh;
+        const float disc = fmaf(bq, bq, -4.0f * aQ * cq);
+        const float delta = (-2.0f * cq) / (bq + sqrtf(fmaxf(disc, 0.0f)));
+        ff yn = ff_add_f(ff_make(yh, yl), delta);
+        bool check = track && cnoise * A <= 2e-8f * ws.hi;
+        if (!(ff_gt(yn, lo) && ff_gt(hi, yn))) {
+            yn = isinf(hi.hi) ? ff_make(2.0f * yh, 0.0f) : ff_mul_f(ff_add(lo, hi), 0.5f);
+            check = false;
+        }
+        if (yn.hi == yh && yn.lo == yl) {                    // no representable progress
+            Cf = C;
+            break;
+        }
+        const float Cm = C, aQm = aQ;
+        const ff ym = ff_make(yh, yl);
+        yh = yn.hi;
+        yl = yn.lo;
+        if (check) {
+            // does any entry change activity at y?  Chunk by chunk, writing
+            // x^{k+1} behind the check while nothing has changed
+            const bool wr = spec;
+            spec = false;
+            const float dsave = dx2;
+            bool chg = false;
+            int cw = 0;
+            for (int c = 0; c < nch; c++) {
+                load_chunk(c);
+                bool cc = false;
+#pragma unroll
+                for (int k = 0; k < kSlots; k++) {
+                    rtd[k] = td_at(k, yh, yl);
+                    const bool a = rtd[k] < rx[k] && rj[k] >= 0;
+                    cc |= a != ((act & bit(c, k)) != 0ull);
+                }
+                if (__any_sync(0xffffffffu, cc)) {
+                    chg = true;
+                    break;
+                }
+                if (wr) {
+                    write_chunk(c, false);
+                    cw = c + 1;
+                }
+            }
+            if (!chg) {
+                const float dy = (yh - ym.hi) + (yl - ym.lo);
+                Cf = Cm - aQm * dy;
+                written = wr;
+                break;
+            }
+            if (wr) {
+                undo_chunks(cw, yh, yl);
+                dx2 = dsave;
+            }
+        }
+        // evaluation at y
+        C = A = Q = 0.0f;
+        act = 0ull;
+        for (int c = 0; c < nch; c++) {
+            load_chunk(c);
+#pragma unroll
+            for (int k = 0; k < kSlots; k++) {
+                const float u = ru[k];
+                const float td = td_at(k, yh, yl);
+                rtd[k] = td;
+                const float cr = fminf(td, rx[k]);
+                C = fmaf(u, cr, C);
+                A = fmaf(u, fabsf(cr), A);
+                if (td < rx[k] && rj[k] >= 0) {
+                    Q = fmaf(u, u, Q);
+                    act |= bit(c, k);
+                }
+            }
+        }
+        C = group_sum<32>(C);
+        A = group_sum<32>(A);
+        Q = group_sum<32>(Q);
+    }
+    if (lane == 0) {
+        t_out[row] = ((double)s0.hi + (double)s0.lo) - (double)Cf;
+        evals += nev;
+    }
+    if (written) return;
+    // ---- new iterate at the final y, column sums ----
+    for (int c = 0; c < nch; c++) {
+        load_chunk(c);
+#pragma unroll
+        for (int k = 0; k < kSlots; k++) rtd[k] = td_at(k, yh, yl);
+        write_chunk(c, false);
     }
 }
 
@@ -342,14 +542,13 @@ __device__ void row_mixed(const DevMarket& mk, const float* __restrict__ U, cons
                           float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
                           unsigned long long* acc_s, unsigned long long* acc_g, double* __restrict__ t_out,
                           const RowCtx& rc, int row, bool valid, float& dx2, int& capped, int& evals) {
-    RowRegs R;
     if (LONG) {
-        R.b = valid ? mk.rp[row] : 0;
-        R.e = valid ? mk.rp[row + 1] : 0;
+        row_mixed_long(mk, U, Xin, Xout, Xb, pff, pff, acc_s, acc_g, t_out, rc, row, valid, dx2, capped, evals);
     } else {
+        RowRegs R;
         row_load<G>(mk, U, Xin, row, valid, R);
+        row_mixed_core<G>(mk, U, Xin, Xout, Xb, pff, pff, acc_s, acc_g, t_out, rc, row, valid, dx2, capped, evals, R);
     }
-    row_mixed_core<G, LONG>(mk, U, Xin, Xout, Xb, pff, pff, acc_s, acc_g, t_out, rc, row, valid, dx2, capped, evals, R);
 }
 
 // ---------------------------------------------------------------------------
