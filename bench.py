@@ -435,6 +435,7 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / avg_prox_s / 1e9
     kkt_now = info.kkt
+    evals_per_row = (info.row_solve_evals - info0.row_solve_evals) / max(mk.n * prox_launches, 1)
     capi.pdhcg_fisher_end(solver.h, None, None, None, None)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -481,7 +482,8 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": workload_name(cfg), "n": mk.n, "m": mk.m, "nnz": mk.nnz,
                    "iters_per_step": prm.kkt_check_every, "accepted_iters": iters, "row_passes": passes,
-                   "kkt_after_timed_steps": kkt_now, "l2": "inputs (24 GB/pass) far above L2 (129 MB)",
+                   "kkt_after_timed_steps": kkt_now, "row_equation_evals_per_row_pass": round(evals_per_row, 3),
+                   "l2": "inputs (24 GB/pass) far above L2 (129 MB)",
                    "generate_s": round(t_gen, 1)},
         "roofline": {"bound": "hbm", "kernel": "prox_kernel (row subproblems + column sums + averaging)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
