@@ -15,8 +15,6 @@
 // The row solver itself (rowsolve.cuh) replaces the paper's 32-section search
 // (a GPU design for H100) by an exact finite procedure; the paper's searches
 // remain in the oracle.
-#include <climits>
-
 #include "common.cuh"
 #include "rowsolve.cuh"
 
@@ -25,66 +23,41 @@ namespace pdhcg {
 // ---------------------------------------------------------------------------
 // the persistent row kernel
 // ---------------------------------------------------------------------------
-// One grab of register-resident rows (MIXED): units [base, uend) of bucket
-// bk.  While one unit is solved the next unit's (good id, utility, x^k) are
-// already being loaded (software prefetch).
+// One bucket of register-resident rows (MIXED): each warp takes chunks of
+// units from the bucket's counter; while one unit is solved the next unit's
+// (good id, utility, x^k) are already being loaded (software prefetch).
 template <int G>
-__device__ void grab_mixed(const DevMarket& mk, const Bucket& bk, int base, int uend, const void* Xin, void* Xout,
-                           const IterBufs& bf, const float2* sp, unsigned long long* acc_s, const RowCtx& rc,
-                           float& dxf, int& capped, int& evals) {
+__device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned long long* counter, const void* Xin,
+                             void* Xout, const IterBufs& bf, const float2* sp, unsigned long long* acc_s,
+                             const RowCtx& rc, float& dxf, int& capped, int& evals) {
     constexpr int rpw = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int count = (int)bk.count;
-    const int* __restrict__ ro = mk.row_order + bk.first;
+    const long long units = (bk.count + rpw - 1) / rpw;
     const float* U = (const float*)mk.uv;
     const float* Xi = (const float*)Xin;
-    int slot = base * rpw + lane / G;
-    bool vn = slot < count;
-    int rn = vn ? __ldg(ro + slot) : 0;
-    RowRegs nx;
-    row_load<G>(mk, U, Xi, rn, vn, nx);
-    for (int u = base; u < uend; u++) {
-        RowRegs cr = nx;
-        const int rc_row = rn;
-        const bool vc = vn;
-        if (u + 1 < uend) {
-            slot = (u + 1) * rpw + lane / G;
-            vn = slot < count;
-            rn = vn ? __ldg(ro + slot) : 0;
-            row_load<G>(mk, U, Xi, rn, vn, nx);
-        }
-        row_mixed_core<G>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc, rc_row, vc,
-                          dxf, capped, evals, cr);
-    }
-}
-
-// One grab of chunked rows (MIXED) or of rows of any width (FP64).
-template <bool MIXED>
-__device__ void grab_rows(const DevMarket& mk, const Bucket& bk, int base, int uend, const void* Xin, void* Xout,
-                          const IterBufs& bf, const float2* sp, unsigned long long* acc_s, const RowCtx& rc,
-                          float& dxf, double& dxd, int& capped, int& evals) {
-    const int lane = threadIdx.x & 31;
-    const int g = bk.g;
-    const int rpw = 32 / g;
-    const int count = (int)bk.count;
-    const int* __restrict__ ro = mk.row_order + bk.first;
-    for (int u = base; u < uend; u++) {
-        const int slot = u * rpw + lane / g;
-        const bool valid = slot < count;
-        const int row = valid ? ro[slot] : 0;
-        if (MIXED) {
-            row_mixed_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff, sp,
-                           acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped, evals);
-        } else {
-            const double* U = (const double*)mk.uv;
-            double* Xo = (double*)Xout;
-            const double* Xi = (const double*)Xin;
-            double* Xb = (double*)bf.Xb;
-            if (bk.chunks) row_fp64<32, true>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-            else if (g == 4) row_fp64<4, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-            else if (g == 8) row_fp64<8, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-            else if (g == 16) row_fp64<16, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
-            else row_fp64<32, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, 16ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= units) break;
+        const long long uend = min((long long)base + 16, units);
+        long long slot = (long long)base * rpw + lane / G;
+        bool vn = slot < bk.count;
+        int rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
+        RowRegs nx;
+        row_load<G>(mk, U, Xi, rn, vn, nx);
+        for (long long u = (long long)base; u < uend; u++) {
+            RowRegs cr = nx;
+            const int rc_row = rn;
+            const bool vc = vn;
+            if (u + 1 < uend) {
+                slot = (u + 1) * rpw + lane / G;
+                vn = slot < bk.count;
+                rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
+                row_load<G>(mk, U, Xi, rn, vn, nx);
+            }
+            row_mixed_core<G>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
+                                     rc_row, vc, dxf, capped, evals, cr);
         }
     }
 }
@@ -119,43 +92,46 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     double dxd = 0.0;
     int capped = 0, evals = 0;
 
-    // Each warp takes its next grab from the bucket whose cursor is furthest
-    // back in memory.  The rows of a bucket are stored in memory order, so the
-    // buckets advance through the CSR arrays side by side, and rows that are
-    // neighbours in memory (usually of different buckets) are solved close
-    // together in time and share the cache lines at their boundary.
-    while (true) {
-        int key = INT_MAX;     // row at the cursor of bucket `lane`
-        if (lane < mk.nb) {
-            const Bucket bk = mk.buckets[lane];
-            const int rpw = 32 / bk.g;
-            const long long units = (bk.count + rpw - 1) / rpw;
-            const long long c = (long long)*(volatile unsigned long long*)&ctl->work[lane];
-            if (c < units) key = __ldg(mk.row_order + bk.first + c * rpw);
-        }
-        int kmin = key;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        if (kmin == INT_MAX) break;
-        const int bi = __ffs(__ballot_sync(0xffffffffu, key == kmin)) - 1;
+    for (int bi = 0; bi < mk.nb; bi++) {
         const Bucket bk = mk.buckets[bi];
-        const int units = (int)((bk.count + 32 / bk.g - 1) / (32 / bk.g));
-        const int grab = bk.chunks ? 1 : 16;       // units taken per atomic
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(&ctl->work[bi], (unsigned long long)grab);
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (got >= (unsigned long long)units) continue;      // emptied meanwhile: choose again
-        const int base = (int)got;
-        const int uend = min(base + grab, units);
+        const int g = bk.g;
         if (MIXED && !bk.chunks) {
-            switch (bk.g) {
-                case 4: grab_mixed<4>(mk, bk, base, uend, Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
-                case 8: grab_mixed<8>(mk, bk, base, uend, Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
-                case 16: grab_mixed<16>(mk, bk, base, uend, Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
-                default: grab_mixed<32>(mk, bk, base, uend, Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+            switch (g) {
+                case 4: bucket_mixed<4>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                case 8: bucket_mixed<8>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                case 16: bucket_mixed<16>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                default: bucket_mixed<32>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
             }
-        } else {
-            grab_rows<MIXED>(mk, bk, base, uend, Xin, Xout, bf, sp, acc_s, rc, dxf, dxd, capped, evals);
+            continue;
+        }
+        const int rpw = 32 / g;
+        const long long units = (bk.count + rpw - 1) / rpw;
+        const long long grab = bk.chunks ? 1 : 16;       // units taken per atomic
+        while (true) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctl->work[bi], (unsigned long long)grab);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((long long)base >= units) break;
+            const long long uend = min((long long)base + grab, units);
+            for (long long u = (long long)base; u < uend; u++) {
+                long long slot = u * rpw + lane / g;
+                bool valid = slot < bk.count;
+                int row = valid ? mk.row_order[bk.first + slot] : 0;
+                if (MIXED) {
+                    row_mixed_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff,
+                                   sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped, evals);
+                } else {
+                    const double* U = (const double*)mk.uv;
+                    double* Xo = (double*)Xout;
+                    const double* Xi = (const double*)Xin;
+                    double* Xb = (double*)bf.Xb;
+                    if (bk.chunks) row_fp64<32, true>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else if (g == 4) row_fp64<4, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else if (g == 8) row_fp64<8, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else if (g == 16) row_fp64<16, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                    else row_fp64<32, false>(mk, U, Xi, Xo, Xb, bf.pc, acc_s, bf.acc, bf.t, rc, row, valid, dxd, capped);
+                }
+            }
         }
     }
 
