@@ -89,6 +89,9 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
     CK(ensure(h->ad_p, m * sizeof(double)));
     CK(ensure(h->p0i, m * sizeof(double)));
     const double sum_w0 = device_sum((const double*)h->w.p, n, h->part2, s);
+    // budgets in caller row order (ad_w); h->w holds them in the internal row order
+    const int* perm = (const int*)h->perm.p;
+    k_rows_to_caller(n, perm, (const double*)h->w.p, nullptr, (double*)h->ad_w.p, s);
     long long iters = 0, passes = 0, capped = 0, evals = 0;
     int restarts = 0, outer = 0;
     double solve_ms = 0.0, setup_ms = 0.0;
@@ -114,7 +117,7 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
         const double sum_wn = device_sum((const double*)h->ad_wn.p, n, h->part2, s);
         if (!(sum_wn > 0.0) || !std::isfinite(sum_wn)) return PDHCG_ERR_NUMERIC;
         const int nb = 256;
-        rescale_change_kernel<<<nb, 256, 0, s>>>(n, (double*)h->ad_wn.p, sum_w0 / sum_wn, (const double*)h->w.p,
+        rescale_change_kernel<<<nb, 256, 0, s>>>(n, (double*)h->ad_wn.p, sum_w0 / sum_wn, (const double*)h->ad_w.p,
                                                  (double*)h->part2.p);
         std::vector<double> part(2 * nb);
         CK(cudaMemcpyAsync(part.data(), h->part2.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -128,7 +131,8 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
         CK(cudaMemcpyAsync(h->p0i.p, r.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (r.x != h->X0.p) CK(cudaMemcpyAsync(h->X0.p, r.x, P.nnz * vb, cudaMemcpyDeviceToDevice, s));
         // budgets for the next round (the fixed-point map)
-        CK(cudaMemcpyAsync(h->w.p, h->ad_wn.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->ad_w.p, h->ad_wn.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        k_rows_to_internal(n, perm, (const double*)h->ad_wn.p, (double*)h->w.p, s);
         if (!std::isfinite(change)) return PDHCG_ERR_NUMERIC;
         if (change < outer_tol) {
             out = (st == PDHCG_OK) ? PDHCG_OK : PDHCG_ERR_NOT_CONVERGED;
@@ -142,7 +146,7 @@ pdhcg_status pdhcg_ad_solve(pdhcg_handle h, const pdhcg_market* mk, const int64_
     double* wd = (double*)out_loc(h->o_u, w_out, n * sizeof(double), &e2);
     CK(e2);
     CK(cudaMemcpyAsync(pd, h->ad_p.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (wd) CK(cudaMemcpyAsync(wd, h->w.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (wd) CK(cudaMemcpyAsync(wd, h->ad_w.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(copy_out(p_out, pd, m * sizeof(double), s));
     CK(copy_out(w_out, wd, n * sizeof(double), s));
     CK(cudaStreamSynchronize(s));

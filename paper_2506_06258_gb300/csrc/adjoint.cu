@@ -463,8 +463,10 @@ pdhcg_status adjoint_core(pdhcg_handle h, const AdjArgs& a, const double* r, con
 __global__ void scatter_int_kernel(int m, const int* rank, const double* src, double* dst) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) dst[rank[j]] = src[j];
 }
-__global__ void gather_int_kernel(int m, const int* rank, const double* src, double* dst) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) dst[j] = src[rank[j]];
+// Arrow-Debreu budgets at the fixed point: agent j (caller row j) owns caller
+// good j, so w_j = p_j, stored at internal row inv[j]
+__global__ void ad_weq_kernel(int m, const int* rank, const int* inv, const double* p_int, double* w_eq) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) w_eq[inv[j]] = p_int[rank[j]];
 }
 __global__ void axpy_const_kernel(int m, double* v, double c) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) v[j] += c;
@@ -537,14 +539,25 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
     CK(ensure(B[11], n * sizeof(double)));
     CK(ensure(B[12], n * sizeof(double)));
     CK(ensure(B[13], 4 * (size_t)(n + m) * sizeof(double)));
+    CK(ensure(B[17], n * sizeof(double)));
+    CK(ensure(B[18], nnz * sizeof(double)));
     double* r_int = (double*)B[10].p;
     double* w_eq = (double*)B[11].p;
-    if (!gw) gw = (double*)B[12].p;
+    // the derivative is computed in the internal row order (rows stored bucket
+    // by bucket) and mapped back to the caller's rows and entries at the end
+    const int* perm = (const int*)h->perm.p;
+    double* gw_int = (double*)B[12].p;
+    double* gu_int = (double*)B[18].p;
+    double* gt_int = nullptr;
+    if (gt) {
+        gt_int = (double*)B[17].p;
+        k_rows_to_internal(n, perm, gt, gt_int, s);
+    }
     scatter_int_kernel<<<gsz(m), 256, 0, s>>>(m, (const int*)h->rank.p, gp, r_int);
     const SolveResult& R = st.res;
     if (st.kind == 1) {
         // budgets at the fixed point are the prices of the own goods: w_i = p_i
-        gather_int_kernel<<<gsz(m), 256, 0, s>>>(m, (const int*)h->rank.p, R.p, w_eq);
+        ad_weq_kernel<<<gsz(m), 256, 0, s>>>(m, (const int*)h->rank.p, (const int*)h->inv.p, R.p, w_eq);
     } else {
         CK(cudaMemcpyAsync(w_eq, h->w.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
@@ -584,13 +597,13 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
         // components of the tight graph (one derivative pass computes them)
         double res0;
         int ne0, kc0;
-        pdhcg_status r0 = adjoint_core(h, a, r_int, nullptr, gu, gw, 1, &res0, &ne0, &kc0, nullptr);
+        pdhcg_status r0 = adjoint_core(h, a, r_int, nullptr, gu_int, gw_int, 1, &res0, &ne0, &kc0, nullptr);
         if (r0 != PDHCG_OK && r0 != PDHCG_ERR_NOT_CONVERGED) return r0;
         const int* label = (const int*)h->adj[4].p;
         const double* Pc = (const double*)h->adj[5].p + nv;
         {
             std::vector<int> agent_row(m);
-            for (int j = 0; j < m; j++) agent_row[P.rank[j]] = j;     // internal good -> caller row
+            for (int j = 0; j < m; j++) agent_row[P.rank[j]] = P.inv[j];     // internal good -> its owner's internal row
             CK(cudaMemcpyAsync(B[15].p, agent_row.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
         }
         const int* agent_row = (const int*)B[15].p;
@@ -652,10 +665,12 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
     }
     double res;
     int ne, kc;
-    pdhcg_status r = adjoint_core(h, a, r_int, gt, gu, gw, 200000, &res, &ne, &kc, nullptr);
+    pdhcg_status r = adjoint_core(h, a, r_int, gt_int, gu_int, gw_int, 200000, &res, &ne, &kc, nullptr);
     if (r != PDHCG_OK && r != PDHCG_ERR_NOT_CONVERGED) return r;
+    k_entries(n, perm, (const long long*)h->urp.p, (const long long*)h->rp.p, gu_int, gu, 8, true, s);
+    if (gw) k_rows_to_caller(n, perm, gw_int, nullptr, gw, s);
     CK(copy_out(grad_u, gu, nnz * sizeof(double), s));
-    CK(copy_out(grad_w, gw, n * sizeof(double), s));
+    if (gw) CK(copy_out(grad_w, gw, n * sizeof(double), s));
     CK(cudaStreamSynchronize(s));
     return r;
 }

@@ -74,7 +74,7 @@ struct KktPart {
 struct Bucket {
     int g;          // lanes per row (4, 8, 16, 32)
     int chunks;     // 0 = row fits in registers (g * kSlots), else multi-chunk
-    long long first, count;   // range in row_order
+    long long first, count;   // internal rows [first, first + count)
 };
 
 // ---------------------------------------------------------------------------
@@ -265,14 +265,16 @@ __device__ __forceinline__ double row_scale(double mx) {
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in prox.cu, kkt.cu, prep.cu)
 // ---------------------------------------------------------------------------
+// The preprocessed market (single-market solver): rows stored bucket by bucket
+// (internal row r is caller row perm[r]; the row kernel solves one bucket after
+// another, so it streams the arrays in order), goods relabelled by degree.
 struct DevMarket {
     int n, m;
     long long nnz;
-    const long long* rp;
+    const long long* rp;   // internal row pointer
     const int* cj;
     const void* uv;        // float or double
     const double* w;
-    const int* row_order;  // rows grouped by degree bucket
     Bucket buckets[kMaxBuckets];
     int nb;
     int hot;               // goods [0, hot) accumulate in shared memory

@@ -44,10 +44,12 @@ __global__ void col_degree_kernel(long long nnz, const int* __restrict__ col, in
     }
 }
 
-// row scale (row_scale), scaled utilities, relabelled goods, initial x
+// row scale (row_scale), scaled utilities, relabelled goods, initial x; caller
+// row i is written as internal row inv[i], whose entries start at irp[inv[i]]
 template <typename V>
 __global__ void scale_kernel(int n, const long long* __restrict__ rp, const int* __restrict__ col, const void* val,
                              int val_f32, const int* __restrict__ rank, const int* __restrict__ deg,
+                             const int* __restrict__ inv, const long long* __restrict__ irp,
                              double* __restrict__ rowmax, V* __restrict__ uv, int* __restrict__ cj,
                              V* __restrict__ x0, int init_x) {
     const int lane = threadIdx.x & 31;
@@ -55,19 +57,50 @@ __global__ void scale_kernel(int n, const long long* __restrict__ rp, const int*
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long i = gw; i < n; i += nw) {
         const long long b = rp[i], e = rp[i + 1];
+        const int r = inv[i];
+        const long long ib = irp[r] - b;       // internal index = caller index + ib
         double mx = 0.0;
         for (long long q = b + lane; q < e; q += 32) {
             const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
             mx = fmax(mx, u);
         }
         mx = row_scale<V>(warp_max_d(mx));
-        if (lane == 0) rowmax[i] = mx;
+        if (lane == 0) rowmax[r] = mx;
         for (long long q = b + lane; q < e; q += 32) {
             const double u = val_f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
-            uv[q] = (V)(u / mx);
+            uv[q + ib] = (V)(u / mx);
             const int j = col[q];
-            cj[q] = rank[j];
-            if (init_x) x0[q] = (V)(1.0 / (double)deg[j]);
+            cj[q + ib] = rank[j];
+            if (init_x) x0[q + ib] = (V)(1.0 / (double)deg[j]);
+        }
+    }
+}
+
+// internal row r <-> caller row perm[r]: dst[perm[r]] = src[r] (times mul[r])
+__global__ void rows_to_caller_kernel(int n, const int* __restrict__ perm, const double* __restrict__ src,
+                                      const double* __restrict__ mul, double* __restrict__ dst) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        dst[perm[r]] = mul ? src[r] * mul[r] : src[r];
+}
+__global__ void rows_to_internal_kernel(int n, const int* __restrict__ perm, const double* __restrict__ src,
+                                        double* __restrict__ dst) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) dst[r] = src[perm[r]];
+}
+// per-entry arrays: internal row r holds entries [irp[r], irp[r+1]), the same
+// entries as caller row perm[r] from crp[perm[r]] on, in the same order
+template <typename V>
+__global__ void entries_kernel(int n, const int* __restrict__ perm, const long long* __restrict__ crp,
+                               const long long* __restrict__ irp, const V* __restrict__ src, V* __restrict__ dst,
+                               int to_caller) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = gw; r < n; r += nw) {
+        const long long ib = irp[r], d = irp[r + 1] - ib;
+        const long long cb = crp[perm[r]];
+        for (long long k = lane; k < d; k += 32) {
+            if (to_caller) dst[cb + k] = src[ib + k];
+            else dst[ib + k] = src[cb + k];
         }
     }
 }
@@ -84,9 +117,6 @@ __global__ void gather_goods_kernel(int m, const int* __restrict__ rank, const d
 __global__ void scatter_goods_kernel(int m, const int* __restrict__ rank, const double* __restrict__ src_orig,
                                      double* __restrict__ dst_int) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) dst_int[rank[j]] = src_orig[j];
-}
-__global__ void util_out_kernel(int n, const double* __restrict__ t, const double* __restrict__ rowmax, double* __restrict__ out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = t[i] * rowmax[i];
 }
 template <typename Vs, typename Vd>
 __global__ void convert_kernel(long long n, const Vs* __restrict__ s, Vd* __restrict__ d) {
@@ -128,10 +158,29 @@ void k_col_degree(long long nnz, const int* col, int m, int* deg, cudaStream_t s
     col_degree_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, col, m, deg);
 }
 void k_scale(bool mixed, int n, const long long* rp, const int* col, const void* val, int f32, const int* rank,
-             const int* deg, double* rowmax, void* uv, int* cj, void* x0, int init_x, cudaStream_t s) {
+             const int* deg, const int* inv, const long long* irp, double* rowmax, void* uv, int* cj, void* x0,
+             int init_x, cudaStream_t s) {
     int g = grid_for((long long)n * 32, 256, 8192);
-    if (mixed) scale_kernel<float><<<g, 256, 0, s>>>(n, rp, col, val, f32, rank, deg, rowmax, (float*)uv, cj, (float*)x0, init_x);
-    else scale_kernel<double><<<g, 256, 0, s>>>(n, rp, col, val, f32, rank, deg, rowmax, (double*)uv, cj, (double*)x0, init_x);
+    if (mixed)
+        scale_kernel<float><<<g, 256, 0, s>>>(n, rp, col, val, f32, rank, deg, inv, irp, rowmax, (float*)uv, cj,
+                                              (float*)x0, init_x);
+    else
+        scale_kernel<double><<<g, 256, 0, s>>>(n, rp, col, val, f32, rank, deg, inv, irp, rowmax, (double*)uv, cj,
+                                               (double*)x0, init_x);
+}
+void k_rows_to_caller(int n, const int* perm, const double* src, const double* mul, double* dst, cudaStream_t s) {
+    rows_to_caller_kernel<<<grid_for(n), 256, 0, s>>>(n, perm, src, mul, dst);
+}
+void k_rows_to_internal(int n, const int* perm, const double* src, double* dst, cudaStream_t s) {
+    rows_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, perm, src, dst);
+}
+void k_entries(int n, const int* perm, const long long* crp, const long long* irp, const void* src, void* dst,
+               int bytes, bool to_caller, cudaStream_t s) {
+    int g = grid_for((long long)n * 32, 256, 8192);
+    if (bytes == 4)
+        entries_kernel<float><<<g, 256, 0, s>>>(n, perm, crp, irp, (const float*)src, (float*)dst, to_caller ? 1 : 0);
+    else
+        entries_kernel<double><<<g, 256, 0, s>>>(n, perm, crp, irp, (const double*)src, (double*)dst, to_caller ? 1 : 0);
 }
 void k_fill(double* a, long long n, double v, cudaStream_t s) { fill_kernel<<<grid_for(n), 256, 0, s>>>(a, n, v); }
 void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, cudaStream_t s) {
@@ -159,9 +208,6 @@ void k_max_scaled_t(int n, const long long* rp, const float* uv, const double* t
     max_scaled_t_kernel<<<grid_for((long long)n * 32), 256, 0, s>>>(n, rp, uv, t, out);
 }
 
-void k_util_out(int n, const double* t, const double* rowmax, double* out, cudaStream_t s) {
-    util_out_kernel<<<grid_for(n), 256, 0, s>>>(n, t, rowmax, out);
-}
 void k_convert(long long n, const void* src, bool src_f32, void* dst, bool dst_f32, cudaStream_t s) {
     int g = grid_for(n);
     if (src_f32 && dst_f32) cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, s);

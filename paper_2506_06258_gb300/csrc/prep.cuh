@@ -13,11 +13,18 @@ void k_validate(int n, int m, long long nnz, const long long* rp, const int* col
                 const double* w, unsigned int* err, cudaStream_t s);
 void k_col_degree(long long nnz, const int* col, int m, int* deg, cudaStream_t s);
 void k_scale(bool mixed, int n, const long long* rp, const int* col, const void* val, int f32, const int* rank,
-             const int* deg, double* rowmax, void* uv, int* cj, void* x0, int init_x, cudaStream_t s);
+             const int* deg, const int* inv, const long long* irp, double* rowmax, void* uv, int* cj, void* x0,
+             int init_x, cudaStream_t s);
+// The preprocessed market stores its rows bucket by bucket: internal row r is
+// caller row perm[r].  Conversions between the two orders, per row (doubles;
+// with mul, dst[perm[r]] = src[r] * mul[r]) and per entry (4- or 8-byte values).
+void k_rows_to_caller(int n, const int* perm, const double* src, const double* mul, double* dst, cudaStream_t s);
+void k_rows_to_internal(int n, const int* perm, const double* src, double* dst, cudaStream_t s);
+void k_entries(int n, const int* perm, const long long* crp, const long long* irp, const void* src, void* dst,
+               int bytes, bool to_caller, cudaStream_t s);
 void k_fill(double* a, long long n, double v, cudaStream_t s);
 void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, cudaStream_t s);
 void k_scatter_goods(int m, const int* rank, const double* src, double* dst_int, cudaStream_t s);
-void k_util_out(int n, const double* t, const double* rowmax, double* out, cudaStream_t s);
 void k_max_scaled_t(int n, const long long* rp, const float* uv, const double* t, double* out, cudaStream_t s);
 void k_convert(long long n, const void* src, bool src_f32, void* dst, bool dst_f32, cudaStream_t s);
 int dist_blocks();

@@ -43,7 +43,7 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
         const long long uend = min((long long)base + 16, units);
         long long slot = (long long)base * rpw + lane / G;
         bool vn = slot < bk.count;
-        int rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
+        int rn = vn ? (int)(bk.first + slot) : 0;
         RowRegs nx;
         row_load<G>(mk, U, Xi, rn, vn, nx);
         for (long long u = (long long)base; u < uend; u++) {
@@ -53,7 +53,7 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
             if (u + 1 < uend) {
                 slot = (u + 1) * rpw + lane / G;
                 vn = slot < bk.count;
-                rn = vn ? __ldg(mk.row_order + bk.first + slot) : 0;
+                rn = vn ? (int)(bk.first + slot) : 0;
                 row_load<G>(mk, U, Xi, rn, vn, nx);
             }
             row_mixed_core<G>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
             for (long long u = (long long)base; u < uend; u++) {
                 long long slot = u * rpw + lane / g;
                 bool valid = slot < bk.count;
-                int row = valid ? mk.row_order[bk.first + slot] : 0;
+                int row = valid ? (int)(bk.first + slot) : 0;
                 if (MIXED) {
                     row_mixed_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff,
                                    sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped, evals);

@@ -147,11 +147,10 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     const void* val = stage_in(h->in_val, mk->val, nnz * (f32 ? 4 : 8), s, &err);
     const double* w = (const double*)stage_in(h->in_w, mk->w, n * sizeof(double), s, &err);
     CK(err);
-    // our own copies of row_ptr and w (the caller's buffers are not kept)
-    CK(ensure(h->rp, (n + 1 + 2) * sizeof(long long)));   // +2: bulk copies read whole 16-byte pairs
-    CK(ensure(h->w, (n + 2) * sizeof(double)));
-    CK(cudaMemcpyAsync(h->rp.p, rp, (n + 1) * sizeof(long long), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(h->w.p, w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // our own copy of the caller's row_ptr (the caller's buffers are not kept):
+    // outputs per entry are mapped back through it
+    CK(ensure(h->urp, (n + 1) * sizeof(long long)));
+    CK(cudaMemcpyAsync(h->urp.p, rp, (n + 1) * sizeof(long long), cudaMemcpyDeviceToDevice, s));
     // validation
     CK(ensure(h->err, 16));
     CK(cudaMemsetAsync(h->err.p, 0, 16, s));
@@ -194,7 +193,10 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     D.nnz = nnz;
     D.nb = 0;
     D.mixed = mixed ? 1 : 0;
-    std::vector<int> row_order;
+    // rows stored bucket by bucket (caller order within a bucket): internal row
+    // r is caller row perm[r], so the row kernel, which solves one bucket after
+    // another, streams the arrays in memory order
+    std::vector<int> perm;
     {
         // rows by degree bucket
         const int caps[4] = {4 * kSlots, 8 * kSlots, 16 * kSlots, 32 * kSlots};
@@ -211,10 +213,10 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
         }
         std::vector<long long> start(5, 0);
         for (int b = 1; b < 5; b++) start[b] = start[b - 1] + cnt[b - 1];
-        row_order.assign(n, 0);
+        perm.assign(n, 0);
         {
             std::vector<long long> pos = start;
-            for (int i = 0; i < n; i++) row_order[pos[bk[i]]++] = i;
+            for (int i = 0; i < n; i++) perm[pos[bk[i]]++] = i;
         }
         for (int b = 0; b < 5; b++) {
             if (!cnt[b]) continue;
@@ -226,10 +228,19 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
             D.buckets[D.nb++] = B;
         }
     }
-    CK(ensure(h->row_order, std::max<size_t>(row_order.size(), 1) * sizeof(int)));
-    if (!row_order.empty())
-        CK(cudaMemcpyAsync(h->row_order.p, row_order.data(), row_order.size() * sizeof(int), cudaMemcpyHostToDevice,
-                           s));
+    P.inv.assign(n, 0);
+    for (int r = 0; r < n; r++) P.inv[perm[r]] = r;
+    std::vector<long long> irp(n + 1);
+    irp[0] = 0;
+    for (int r = 0; r < n; r++) irp[r + 1] = irp[r] + (rph[perm[r] + 1] - rph[perm[r]]);
+    CK(ensure(h->perm, n * sizeof(int)));
+    CK(ensure(h->inv, n * sizeof(int)));
+    CK(ensure(h->rp, (n + 1 + 2) * sizeof(long long)));   // +2: bulk copies read whole 16-byte pairs
+    CK(ensure(h->w, (n + 2) * sizeof(double)));
+    CK(cudaMemcpyAsync(h->perm.p, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->inv.p, P.inv.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->rp.p, irp.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+    k_rows_to_internal(n, (const int*)h->perm.p, w, (double*)h->w.p, s);
     // scaled utilities, relabelled goods, initial x
     const size_t vb = mixed ? 4 : 8;
     CK(ensure(h->cj, (nnz + kPadEntries) * sizeof(int)));
@@ -239,13 +250,13 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     CK(ensure(h->degint, m * sizeof(int)));
     CK(cudaMemcpyAsync(h->degint.p, P.deg_int.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
     k_scale(mixed, n, rp, col, val, f32 ? 1 : 0, (const int*)h->rank.p, (const int*)h->deg.p,
-            (double*)h->rowmax.p, h->uv.p, (int*)h->cj.p, h->X0.p, init_x ? 1 : 0, s);
+            (const int*)h->inv.p, (const long long*)h->rp.p, (double*)h->rowmax.p, h->uv.p, (int*)h->cj.p, h->X0.p,
+            init_x ? 1 : 0, s);
     CK(cudaGetLastError());
     D.rp = (const long long*)h->rp.p;
     D.cj = (const int*)h->cj.p;
     D.uv = h->uv.p;
     D.w = (const double*)h->w.p;
-    D.row_order = (const int*)h->row_order.p;
     // hot goods in shared memory: as many as fit, but flushing them (blocks x
     // hot atomics) must stay small against nnz
     long long hot = std::min<long long>(m, mixed ? 4096 : 8192);
@@ -729,8 +740,9 @@ pdhcg_status write_outputs(pdhcg_handle h, const SolveResult& r, double* p_out, 
     void* xd = out_loc(h->o_x, x_out, P.nnz * vb, &err);
     CK(err);
     if (pd) k_gather_goods(P.m, (const int*)h->rank.p, r.p, pd, s);
-    if (ud) k_util_out(P.n, r.t, (const double*)h->rowmax.p, ud, s);
-    if (xd) CK(cudaMemcpyAsync(xd, r.x, P.nnz * vb, cudaMemcpyDeviceToDevice, s));
+    if (ud) k_rows_to_caller(P.n, (const int*)h->perm.p, r.t, (const double*)h->rowmax.p, ud, s);
+    if (xd) k_entries(P.n, (const int*)h->perm.p, (const long long*)h->urp.p, (const long long*)h->rp.p, r.x, xd,
+                      (int)vb, true, s);
     CK(copy_out(p_out, pd, P.m * sizeof(double), s));
     CK(copy_out(util_out, ud, P.n * sizeof(double), s));
     CK(copy_out(x_out, xd, P.nnz * vb, s));
@@ -776,7 +788,8 @@ pdhcg_status pdhcg_fisher_begin(pdhcg_handle h, const pdhcg_market* mk, const pd
     if (x0) {
         const void* xd = stage_in(h->in_x0, x0, P.nnz * (mixed ? 4 : 8), s, &err);
         CK(err);
-        CK(cudaMemcpyAsync(h->X0.p, xd, P.nnz * (mixed ? 4 : 8), cudaMemcpyDeviceToDevice, s));
+        k_entries(P.n, (const int*)h->perm.p, (const long long*)h->urp.p, (const long long*)h->rp.p, xd, h->X0.p,
+                  mixed ? 4 : 8, false, s);
     }
     const double* p0i = nullptr;
     if (p0) {
@@ -860,12 +873,21 @@ pdhcg_status pdhcg_row_prox(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precis
     double* co = (double*)out_loc(h->o_p, c_out, P.m * sizeof(double), &err);
     CK(err);
     CK(cudaMemsetAsync(h->acc.p, 0, P.m * sizeof(unsigned long long), s));
-    launch_prox_fixed(mixed, P.dm, xi, xo, (const double*)h->p0i.p, tau, (unsigned long long*)h->acc.p,
+    // x in the internal row order: X0 in, X1 out
+    const int* perm = (const int*)h->perm.p;
+    const long long* urp = (const long long*)h->urp.p;
+    k_entries(P.n, perm, urp, P.dm.rp, xi, h->X0.p, (int)vb, false, s);
+    launch_prox_fixed(mixed, P.dm, h->X0.p, h->X1.p, (const double*)h->p0i.p, tau, (unsigned long long*)h->acc.p,
                       (double*)h->t.p, (double*)h->c_cur.p, (double*)h->part.p, (Ctl*)h->ctl.p, s);
     CK(cudaGetLastError());
+    k_entries(P.n, perm, urp, P.dm.rp, h->X1.p, xo, (int)vb, true, s);
     if (so) {
-        if (mixed) k_max_scaled_t(P.n, (const long long*)P.dm.rp, (const float*)P.dm.uv, (const double*)h->t.p, so, s);
-        else CK(cudaMemcpyAsync(so, h->t.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (mixed) {
+            k_max_scaled_t(P.n, P.dm.rp, (const float*)P.dm.uv, (const double*)h->t.p, (double*)h->t_avg.p, s);
+            k_rows_to_caller(P.n, perm, (const double*)h->t_avg.p, nullptr, so, s);
+        } else {
+            k_rows_to_caller(P.n, perm, (const double*)h->t.p, nullptr, so, s);
+        }
     }
     if (co) k_gather_goods(P.m, (const int*)h->rank.p, (const double*)h->c_cur.p, co, s);
     CK(copy_out(x_new, xo, P.nnz * vb, s));
@@ -898,8 +920,9 @@ pdhcg_status pdhcg_kkt(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precision p
     CK(cudaMemsetAsync(h->M.p, mixed ? 0x7f : 0, P.m * sizeof(double), s));
     CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), s));
     if (mixed) launch_to_ff(P.m, (const double*)h->p0i.p, (float2*)h->pff_p.p, s);
+    k_entries(P.n, (const int*)h->perm.p, (const long long*)h->urp.p, P.dm.rp, xd, h->X0.p, (int)vb, false, s);
     KktBufs kb = kkt_bufs(h, nullptr, nullptr, 0);
-    launch_kkt(mixed, P.dm, xd, (const double*)h->p0i.p, kb, s);
+    launch_kkt(mixed, P.dm, h->X0.p, (const double*)h->p0i.p, kb, s);
     KktOut o;
     CK(cudaMemcpyAsync(&o, h->kout.p, sizeof(KktOut), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
