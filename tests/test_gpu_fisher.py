@@ -14,6 +14,7 @@ import pytest
 from oracle import fisher as F
 from paper_2506_06258_gb300 import synth as S
 from tests.gpu_util import dev, host, ragged_market, torch_cuda
+from tests.golden_data import load_equilibrium
 
 pytestmark = pytest.mark.gpu
 
@@ -92,6 +93,9 @@ def test_config1_fp64_matches_oracle(solver):
     p, t = host(out.p), host(out.util)
     assert np.max(np.abs(p - ref.p) / ref.p) <= 1e-5
     assert np.max(np.abs(t - ref.t) / ref.t) <= 1e-5
+    g = load_equilibrium()          # the certified stored equilibrium of C1
+    assert np.max(np.abs(p - g["p"]) / g["p"]) <= 1e-5
+    assert np.max(np.abs(t - g["t"]) / g["t"]) <= 1e-5
     from oracle import certify
     cert = certify.certificate(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, host(out.x), p)
     assert cert["kkt"] <= 1.5e-8
@@ -104,6 +108,8 @@ def test_config1_mixed_matches_oracle(solver):
     ref = F.pdhcg_solve(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, F.Params(tol=1e-11))
     p = host(out.p)
     assert np.max(np.abs(p - ref.p) / ref.p) <= 1e-5
+    g = load_equilibrium()
+    assert np.max(np.abs(p - g["p"]) / g["p"]) <= 1e-5
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
