@@ -64,3 +64,24 @@ def test_batch_rejects_invalid_market(solver):
     bt.val[int(bt.nnz_off[2]) + 1] = -1.0
     out = solver.solve_batched(bt, tol=1e-6, precision="mixed", check=False)
     assert out.status == capi.PDHCG_ERR_INVALID
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_long_rows_rank_one_closed_form(solver, prec):
+    """Dense rank-one markets with 200-300 goods: every row takes the chunked
+    warp-per-row path of the batched kernel; p_j = b_j sum(w) / sum(b) and
+    t_i = a_i w_i sum(b) / sum(w) hold at any size."""
+    from oracle import closed
+    mks = [S.rank_one_market(n, m, seed=950 + k) for k, (n, m) in enumerate(((40, 300), (25, 200), (60, 260)))]
+    bt = S.concat_markets(mks)
+    if prec == "mixed":
+        bt.val = bt.val.astype(np.float32)
+    out = solver.solve_batched(bt, tol=1e-8 if prec == "fp64" else 2e-7, precision=prec)
+    assert out.status == 0, [i["status"] for i in out.info]
+    p, u = host(out.p), host(out.util)
+    for b, mk in enumerate(mks):
+        p_ref, t_ref = closed.rank_one(mk.meta["a"], mk.meta["b"], mk.w)
+        g0, g1 = bt.good_off[b], bt.good_off[b + 1]
+        r0, r1 = bt.row_off[b], bt.row_off[b + 1]
+        assert np.max(np.abs(p[g0:g1] - p_ref) / p_ref) <= 1e-5, b
+        assert np.max(np.abs(u[r0:r1] - t_ref) / t_ref) <= 1e-5, b
