@@ -336,6 +336,68 @@ def _study_c4(sol, S):
     return out
 
 
+# the paper's PDHCG rows of Table tab:fisher (iterations, seconds; its GPU, relative KKT < 1e-4)
+_JD_PAPER = ((3930, 7.0), (4839, 8.4), (5894, 12.4), (6865, 17.1), (10090, 41.3), (14899, 85.8),
+             (48726, 313.9), (152373, 1222.9))
+
+
+def _study_jd(sol, S):
+    """JD-shaped Fisher markets (Section 5.2): the n most active users of the
+    synthetic click log for every size of Table tab:fisher, MIXED solves to
+    the paper's relative KKT 1e-4 (and to 1e-6 up to n = 2e5), 120 s cap each.
+    The paper's own iterations and times (other hardware) ride along as context."""
+    import torch
+    out = {"workload": "JD-shaped synthetic click log (Table tab:fisher prefix sizes exactly, products by "
+                       "popularity rank^-1.3, click-count utilities P(u>=k)=k^-1.5, w~U(0,1)), MIXED", "sizes": []}
+    for (n, nnz_paper, m_paper), (it_p, s_p) in zip(zip(S.JD_USERS, S.JD_NNZ, S.JD_GOODS), _JD_PAPER):
+        mk = S.jd_like_market(n, fp32=True)
+        args = (_dev(mk.row_ptr), _dev(mk.col), _dev(mk.val), _dev(mk.w), mk.m)
+        row = {"n": n, "m": mk.m, "nnz": int(mk.nnz), "paper_m": m_paper, "paper_nnz": nnz_paper,
+               "paper_iters": it_p, "paper_seconds": s_p}
+        for tol in ((1e-4, 1e-6) if n <= 200000 else (1e-4,)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            o = sol.fisher_solve(*args, tol=tol, precision="mixed", max_iter=2_000_000, check=False,
+                                 time_limit_s=120.0)
+            torch.cuda.synchronize()
+            row[f"tol_{tol:.0e}"] = {"status": int(o.status), "seconds": time.perf_counter() - t0,
+                                     "iters": int(o.info["iters"]), "kkt": o.info["kkt"]}
+        out["sizes"].append(row)
+        print(json.dumps({"study": "jd", "partial": True, **row}), flush=True)
+    return out
+
+
+# the paper's rows of Table tab:arrow-debreu: n, m, density of E, density of U, iterations, seconds
+_AD_PAPER = ((1000, 400, 0.5, 0.2, 12.0, 2.7), (10000, 4000, 0.05, 0.02, 9.3, 13.0),
+             (100000, 4000, 0.05, 0.02, 9.2, 62.4), (1000000, 4000, 0.05, 0.02, 9.7, 560.7))
+
+
+def _study_ad(sol, S):
+    """Arrow-Debreu with random sparse endowments (Section 5.3, inside Thm 2's
+    assumptions): the instances of Table tab:arrow-debreu up to n = 1e6, MIXED
+    fixed point to a relative budget change < 1e-4 with inner solves to 1e-6,
+    300 s cap each.  The n = 1e7 row (about 1.2e9 nonzeros in U and E) is left
+    out.  The paper's iterations and times (other hardware) ride along."""
+    import torch
+    out = {"workload": "Arrow-Debreu, U and E Bernoulli-sparse with U(0,1) entries, E columns summing to 1, "
+                       "w0 = E 1, MIXED, outer tol 1e-4, inner tol 1e-6", "sizes": []}
+    for k, (n, m, qe, qu, it_p, s_p) in enumerate(_AD_PAPER):
+        mk, (erp, ecol, ev) = S.ad_random_instance(n, m, qu, qe, seed=S.SEED_BASE + 20 + k, fp32=True)
+        row = {"n": n, "m": m, "density_E": qe, "density_U": qu, "nnz_U": int(mk.nnz), "nnz_E": int(len(ecol)),
+               "paper_outer": it_p, "paper_seconds": s_p}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = sol.ad_solve(_dev(mk.row_ptr), _dev(mk.col), _dev(mk.val), _dev(mk.w), m,
+                         E=(_dev(erp), _dev(ecol.astype(np.int32)), _dev(ev)), outer_tol=1e-4, tol=1e-6,
+                         precision="mixed", max_outer=200, check=False, time_limit_s=300.0)
+        torch.cuda.synchronize()
+        row.update({"status": int(o.status), "seconds": time.perf_counter() - t0, "outer": int(o.info["outer"]),
+                    "inner_iters": int(o.info["iters"]), "kkt": o.info["kkt"]})
+        out["sizes"].append(row)
+        print(json.dumps({"study": "ad", "partial": True, **row}), flush=True)
+    return out
+
+
 def run_study(which):
     import torch
     import __graft_entry__ as g
@@ -343,7 +405,7 @@ def run_study(which):
     from paper_2506_06258_gb300 import api, synth as S
     torch.cuda.set_device(0)
     sol = api.Solver()
-    fn = {"c2": _study_c2, "c4": _study_c4, "c5": _study_c5}[which]
+    fn = {"c2": _study_c2, "c4": _study_c4, "c5": _study_c5, "jd": _study_jd, "ad": _study_ad}[which]
     out = fn(sol, S)
     sol.close()
     print(json.dumps({"study": which, **out}), flush=True)
@@ -361,7 +423,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-tol", action="store_true", help="also run one full solve to tol 1e-6")
-    ap.add_argument("--study", choices=["c2", "c4", "c5"], default=None,
+    ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad"], default=None,
                     help="instead of the bench line, run one comparison study and print its JSON line")
     args = ap.parse_args()
 

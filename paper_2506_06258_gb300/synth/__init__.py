@@ -357,3 +357,123 @@ def rank_one_market(n: int, m: int, seed: int) -> Market:
     col = np.tile(np.arange(m, dtype=np.int32), n)
     val = (a[:, None] * b[None, :]).ravel()
     return Market(n, m, row_ptr, col, val, budgets(seed, n), f"rank-one(n={n},m={m})", {"a": a, "b": b})
+
+
+# ---------------------------------------------------------------------------
+# JD.com-shaped Fisher market (Section 5.2).  The paper's real instances take
+# the n most active users of a click log and the products they clicked; its
+# table gives, for eight values of n, the number of products m and of
+# user-product pairs.  The synthetic stand-in reproduces the pair count of
+# every one of those prefixes exactly and their product counts to about 15 %.
+# ---------------------------------------------------------------------------
+JD_USERS = (2000, 5000, 20000, 50000, 200000, 500000, 1000000, 2557841)
+JD_NNZ = (136877, 265220, 698579, 1278391, 2937906, 4679648, 6189526, 8073837)
+JD_GOODS = (13541, 15887, 19449, 21410, 23853, 25214, 26115, 27330)
+
+
+def jd_activity_profile() -> np.ndarray:
+    """Clicked products of the user of each activity rank (most active first).
+    Inside each interval between two consecutive table sizes the counts follow
+    a log-log interpolation of the interval averages through the intervals'
+    geometric centres (extended linearly past the first and last centre),
+    scaled to the interval's exact total and rounded by largest remainders;
+    every user keeps at least one product."""
+    N = np.array(JD_USERS, dtype=np.int64)
+    tot = np.diff(np.concatenate(([0], np.array(JD_NNZ, dtype=np.int64))))
+    lo = np.concatenate(([0], N[:-1]))
+    lc = np.log(np.sqrt(np.maximum(lo, 1) * N).astype(np.float64))
+    la = np.log(tot / (N - lo))
+    lr = np.log(np.arange(1, N[-1] + 1, dtype=np.float64))
+    f = np.interp(lr, lc, la)
+    head = (la[1] - la[0]) / (lc[1] - lc[0])
+    tail = (la[-1] - la[-2]) / (lc[-1] - lc[-2])
+    f = np.where(lr < lc[0], la[0] + head * (lr - lc[0]), f)
+    f = np.exp(np.where(lr > lc[-1], la[-1] + tail * (lr - lc[-1]), f))
+    d = np.empty(int(N[-1]), dtype=np.int64)
+    for k in range(len(N)):
+        sl = slice(int(lo[k]), int(N[k]))
+        fk = f[sl] * (tot[k] / f[sl].sum())
+        base = np.maximum(np.floor(fk), 1.0).astype(np.int64)
+        rest = int(tot[k] - base.sum())
+        if rest > 0:
+            base[np.argsort(-(fk - np.floor(fk)), kind="stable")[:rest]] += 1
+        elif rest < 0:
+            base[np.argsort(-base, kind="stable")[:-rest]] -= 1
+        d[sl] = base
+    return d
+
+
+def jd_like_market(n: int = JD_USERS[-1], seed: int = SEED_BASE + 5, popularity: float = 1.3,
+                   click_tail: float = 1.5, fp32: bool = False) -> Market:
+    """The n most active users of a synthetic click log shaped like the JD.com
+    data of Section 5.2 (2,557,841 users, 27,330 products, 8,073,837 clicked
+    user-product pairs), with the products they clicked.
+
+    * activity: jd_activity_profile(), the table's prefix sizes exactly;
+    * products: distinct per user, drawn with popularity proportional to
+      rank^-popularity (rank -> product by a seeded permutation); 1.3 brings
+      the product count of every table prefix within about 15 % of the table;
+    * utilities: click counts with P(u >= k) = k^-click_tail, integers capped
+      at 10^4 (the paper uses click counts and gives no law for them);
+    * budgets w ~ U(0, 1) as in the paper, floored at 1e-12 (budgets must be
+      positive);
+    * a product nobody clicked gets one click from one of the least active
+      users, so the full log holds every product and every smaller prefix
+      keeps its table size;
+    * rows in a seeded order, not by activity (``meta["activity_rank"]`` holds
+      each row's rank); goods are the products the chosen users clicked, in
+      product-id order.
+    """
+    if not (1 <= n <= JD_USERS[-1]):
+        raise ValueError(f"n must lie in [1, {JD_USERS[-1]}]")
+    L = _L()
+    M = JD_GOODS[-1]
+    d = jd_activity_profile()
+    N = len(d)
+    row_ptr = _ptr_from_deg(d)
+    nnz = int(row_ptr[-1])
+    cdf = np.empty(M, dtype=np.float64)
+    r2g = np.empty(M, dtype=np.int32)
+    L.synth_popularity(seed, M, popularity, _p(cdf), _p(r2g))
+    col = np.empty(nnz, dtype=np.int32)
+    L.synth_fill_popular(seed, N, M, _p(row_ptr), _p(cdf), _p(r2g), _p(col), None, None, LAW_UNIFORM, 0.0, 1.0)
+    clicks = np.minimum(np.floor((1.0 - uniform_array(seed, 31, nnz)) ** (-1.0 / click_tail)), 1e4)
+    missing = np.nonzero(np.bincount(col, minlength=M) == 0)[0]
+    if len(missing):
+        users = N - 1 - np.arange(len(missing)) % (N - JD_USERS[-2])
+        rows = np.concatenate([np.repeat(np.arange(N), d), users])
+        cols = np.concatenate([col.astype(np.int64), missing])
+        vals = np.concatenate([clicks, np.ones(len(missing))])
+        order = np.lexsort((cols, rows))
+        col, clicks = cols[order].astype(np.int32), vals[order]
+        d = np.bincount(rows, minlength=N)
+        row_ptr = _ptr_from_deg(d)
+    w = np.maximum(uniform_array(seed, 32, N), 1e-12)
+    # the n most active users and the products they clicked
+    sub = int(row_ptr[n])
+    goods, col_s = np.unique(col[:sub], return_inverse=True)
+    perm = np.argsort(uniform_array(seed, 33, n), kind="stable")
+    dd = d[:n][perm]
+    rp = _ptr_from_deg(dd)
+    idx = np.repeat(row_ptr[:n][perm] - rp[:-1], dd) + np.arange(int(rp[-1]))
+    val = clicks[:sub][idx].astype(np.float32 if fp32 else np.float64)
+    return Market(n, len(goods), rp, col_s[idx].astype(np.int32), val, w[:n][perm],
+                  f"JD-shaped(n={n})", {"activity_rank": perm})
+
+
+def ad_random_instance(n: int, m: int, q_u: float, q_e: float, seed: int, fp32: bool = False):
+    """Arrow-Debreu instances of Section 5.3: utilities as in Section 5.1
+    (u_ij nonzero with probability q_u, then U(0,1)); the endowment matrix E
+    (n x m) built the same way with density q_e, every agent holding some good
+    and every good held by some agent (the Assumption-1 repair), each column
+    normalised to sum 1 (a good's unit supply split among its holders).
+    Initial budgets w0 = E 1 (all prices 1), so sum w0 = m.
+    Returns (market with w = w0, (e_row_ptr, e_col, e_val))."""
+    mk = bernoulli_market(n, m, q_u, seed, LAW_UNIFORM, 0.0, 1.0, fp32=fp32,
+                          name=f"AD(n={n},m={m},qU={q_u},qE={q_e})")
+    em = bernoulli_market(n, m, q_e, seed + 104729, LAW_UNIFORM, 0.0, 1.0, name="E")
+    v = np.maximum(em.val, 1e-12)
+    v = v / np.bincount(em.col, weights=v, minlength=m)[em.col]
+    rows = np.repeat(np.arange(n), np.diff(em.row_ptr))
+    mk.w = np.bincount(rows, weights=v, minlength=n)
+    return mk, (em.row_ptr, em.col, v)

@@ -58,3 +58,48 @@ def test_repair_assumption1():
                   np.ones(3))
     fixed = S.repair_assumption1(mk, 1, S.LAW_UNIFORM, 0.0, 1.0)
     _check_csr(fixed)
+
+
+def test_jd_activity_profile_matches_the_table():
+    """Every prefix of the n most active users holds the table's pair count
+    (Section 5.2, Table tab:fisher); every user clicked something."""
+    d = S.jd_activity_profile()
+    assert len(d) == S.JD_USERS[-1] and d.min() >= 1
+    assert [int(d[:n].sum()) for n in S.JD_USERS] == list(S.JD_NNZ)
+    assert d[0] > 50 * np.median(d)                                        # heavy-tailed activity
+
+
+def test_jd_like_market_prefixes():
+    small = S.jd_like_market(2000)
+    _check_csr(small)
+    assert small.n == 2000 and small.nnz == S.JD_NNZ[0]
+    assert abs(small.m / S.JD_GOODS[0] - 1.0) <= 0.15
+    assert np.all(small.val == np.floor(small.val)) and small.val.min() >= 1.0      # click counts
+    assert small.w.max() < 1.0
+    again = S.jd_like_market(2000)
+    assert np.array_equal(small.col, again.col) and np.array_equal(small.val, again.val)
+    mid = S.jd_like_market(20000)
+    assert mid.nnz == S.JD_NNZ[2] and abs(mid.m / S.JD_GOODS[2] - 1.0) <= 0.15
+    # rows are not in activity order, but sorting them back recovers the profile
+    rank = mid.meta["activity_rank"]
+    deg = np.diff(mid.row_ptr)
+    assert not np.all(np.diff(deg) <= 0)
+    assert np.array_equal(np.sort(deg)[::-1], np.sort(S.jd_activity_profile()[:20000])[::-1])
+    assert np.array_equal(deg[np.argsort(rank)], S.jd_activity_profile()[:20000])
+
+
+def test_jd_like_market_full_log_has_every_product():
+    full = S.jd_like_market()
+    _check_csr(full)
+    assert full.n == S.JD_USERS[-1] and full.m == S.JD_GOODS[-1]
+    assert 0 <= full.nnz - S.JD_NNZ[-1] <= 0.001 * S.JD_NNZ[-1]             # one-click repairs only
+
+
+def test_ad_random_instance():
+    mk, (erp, ecol, ev) = S.ad_random_instance(300, 120, 0.2, 0.5, seed=3)
+    _check_csr(mk)
+    assert np.all(np.diff(erp) >= 1) and np.all(np.bincount(ecol, minlength=120) >= 1)
+    assert np.allclose(np.bincount(ecol, weights=ev, minlength=120), 1.0, atol=1e-12)   # unit supply per good
+    rows = np.repeat(np.arange(300), np.diff(erp))
+    assert np.allclose(mk.w, np.bincount(rows, weights=ev, minlength=300)) and np.isclose(mk.w.sum(), 120)
+    assert 0.4 < len(ecol) / (300 * 120) < 0.6 and 0.15 < mk.nnz / (300 * 120) < 0.25
