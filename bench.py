@@ -398,6 +398,55 @@ def _study_ad(sol, S):
     return out
 
 
+# Table diff_division of the paper: average iteration time (ms) of its K-section row solves on
+# its GPU, K = 2, 4, 8, 16, 32, 64, on the Section 5.1 instances (n, m, density)
+_SECTIONS_PAPER = (((100000, 4000, 0.5), (247.3, 163.2, 131.0, 113.3, 95.9, 172.8)),
+                   ((100000, 4000, 0.2), (93.6, 67.1, 58.0, 50.1, 43.3, 64.6)),
+                   ((100000, 4000, 0.1), (45.4, 30.9, 27.2, 23.4, 19.4, 34.1)),
+                   ((1000000, 4000, 0.05), (188.0, 130.4, 110.5, 99.0, 84.3, 155.9)),
+                   ((1000000, 4000, 0.02), (74.4, 50.6, 43.9, 39.6, 36.1, 68.8)),
+                   ((1000000, 4000, 0.01), (42.7, 34.1, 31.1, 27.6, 26.3, 39.8)))
+
+
+def _study_sections(sol, S):
+    """Average iteration time of the exact row root (FP64 and MIXED) on the
+    instances of Table diff_division (Section 5.1 law: w~U(0,1), u_ij nonzero
+    with the given density, then U(0,1)): 3 check periods of 64 accepted
+    iterations after one warm-up period, CUDA events around them.  The paper's
+    K-section times (other hardware) ride along as context."""
+    import torch
+    from paper_2506_06258_gb300 import capi
+    out = {"workload": "Table diff_division instances (Section 5.1 law), exact row root", "sizes": []}
+    for k, ((n, m, q), paper_ms) in enumerate(_SECTIONS_PAPER):
+        mk = S.paper_synthetic(n, m, q, seed=S.SEED_BASE + 40 + k)
+        row = {"n": n, "m": m, "density": q, "nnz": int(mk.nnz),
+               "paper_ms_per_iter_by_sections": dict(zip(("2", "4", "8", "16", "32", "64"), paper_ms))}
+        rp, col, w = _dev(mk.row_ptr), _dev(mk.col), _dev(mk.w)
+        for prec in ("fp64", "mixed"):
+            val = _dev(mk.val.astype(np.float64 if prec == "fp64" else np.float32))
+            market = sol.market(rp, col, val, w, m)
+            prm = capi.default_params(tol=1e-12, prec=capi.PDHCG_FP64 if prec == "fp64" else capi.PDHCG_MIXED,
+                                      timing=1)
+            st = capi.pdhcg_fisher_begin(sol.h, market, prm, None, None)
+            if st:
+                raise capi.PdhcgError(st, "pdhcg_fisher_begin")
+            i0, i1 = capi.pdhcg_info(), capi.pdhcg_info()
+            capi.pdhcg_fisher_step(sol.h, 1, i0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            capi.pdhcg_fisher_step(sol.h, 3, i1)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            its = i1.iters - i0.iters
+            row[prec] = {"ms_per_iter": 1e3 * dt / max(its, 1), "iters": int(its),
+                         "row_pass_ms": (i1.prox_ms - i0.prox_ms) / max(i1.prox_launches - i0.prox_launches, 1)}
+            capi.pdhcg_fisher_end(sol.h, None, None, None, None)
+            del val
+        out["sizes"].append(row)
+        print(json.dumps({"study": "sections", "partial": True, **row}), flush=True)
+    return out
+
+
 def run_study(which):
     import torch
     import __graft_entry__ as g
@@ -405,7 +454,8 @@ def run_study(which):
     from paper_2506_06258_gb300 import api, synth as S
     torch.cuda.set_device(0)
     sol = api.Solver()
-    fn = {"c2": _study_c2, "c4": _study_c4, "c5": _study_c5, "jd": _study_jd, "ad": _study_ad}[which]
+    fn = {"c2": _study_c2, "c4": _study_c4, "c5": _study_c5, "jd": _study_jd, "ad": _study_ad,
+          "sections": _study_sections}[which]
     out = fn(sol, S)
     sol.close()
     print(json.dumps({"study": which, **out}), flush=True)
@@ -423,7 +473,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-tol", action="store_true", help="also run one full solve to tol 1e-6")
-    ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad"], default=None,
+    ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad", "sections"], default=None,
                     help="instead of the bench line, run one comparison study and print its JSON line")
     args = ap.parse_args()
 
