@@ -429,7 +429,11 @@ pdhcg_status adjoint_core(pdhcg_handle h, const AdjArgs& a, const double* r, con
         rr_kernel<<<nbv, 256, 0, s>>>(nv, rr, part, S);
         cudaMemcpyAsync(&h->host->kout[0], &S->rr, sizeof(double), cudaMemcpyDeviceToHost, s);
         CK(cudaStreamEndCapture(s, &graph));
-        CK(cudaGraphInstantiate(&exec, graph, 0));
+        {
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            if (ie != cudaSuccess) cudaGraphDestroy(graph);
+            CK(ie);
+        }
         for (it = 0; it < max_cg; it += K) {
             cudaError_t ce = cudaGraphLaunch(exec, s);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -645,7 +649,11 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
         }
         cudaMemcpyAsync(&h->host->kout[0], dmax, 16, cudaMemcpyDeviceToHost, s);
         CK(cudaStreamEndCapture(s, &graph));
-        CK(cudaGraphInstantiate(&exec, graph, 0));
+        {
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            if (ie != cudaSuccess) cudaGraphDestroy(graph);
+            CK(ie);
+        }
         bool ok = false;
         for (int it = 0; it < 40000; it += 16) {
             cudaError_t ce = cudaGraphLaunch(exec, s);
