@@ -801,16 +801,19 @@ pdhcg_status pdhcg_fisher_solve_batched(pdhcg_handle h, int32_t B, const int64_t
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
             float ms = 0.0f;
-            for (int rep = 0; rep < 2; rep++) {      // first run warms up
-                CK(cudaMemsetAsync(a.queue, 0, 16, s));
+            cudaError_t te = cudaSuccess;
+            for (int rep = 0; rep < 2 && te == cudaSuccess; rep++) {      // first run warms up
+                te = cudaMemsetAsync(a.queue, 0, 16, s);
+                if (te != cudaSuccess) break;
                 cudaEventRecord(e0, s);
                 launch_solve(mixed, t, std::min<int>(grid, t.B), smem, s);
                 cudaEventRecord(e1, s);
-                CK(cudaEventSynchronize(e1));
-                cudaEventElapsedTime(&ms, e0, e1);
+                te = cudaEventSynchronize(e1);
+                if (te == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
+            CK(te);
             CK(cudaGetLastError());
             if (ms < best_ms) { best_ms = ms; best_g = gq; }
             if (prm->verbose) fprintf(stderr, "[pdhcg-batch] tune class %d g %d: %.3f ms\n", c, gq, ms);
