@@ -51,3 +51,20 @@ def test_random_endowments_general_E():
     r = arrow.ad_fixed_point(mk.row_ptr, mk.col, mk.val, np.ones(n), m, E=E, outer_tol=1e-8, inner_tol=1e-11)
     assert r["converged"]
     assert np.max(np.abs(E @ r["p"] - r["w"]) / r["w"]) < 1e-6
+
+
+def test_generated_random_endowment_instance_reaches_a_certified_fixed_point():
+    """synth.ad_random_instance (the law of Section 5.3) at a small size: the
+    fixed point converges (inside Thm 2's random-E assumptions), budgets equal
+    the value of the endowments at the final prices, and the final Fisher
+    solve passes the equilibrium certificate."""
+    from oracle import certify
+    mk, (erp, ecol, ev) = S.ad_random_instance(40, 16, 0.3, 0.5, seed=12)
+    E = np.zeros((mk.n, mk.m))
+    E[np.repeat(np.arange(mk.n), np.diff(erp)), ecol] = ev
+    r = arrow.ad_fixed_point(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, E=E, outer_tol=1e-9, inner_tol=1e-11)
+    assert r["converged"] and r["outer"] < 60
+    assert np.max(np.abs(E @ r["p"] - r["w"]) / r["w"]) < 1e-6
+    assert np.isclose(r["w"].sum(), mk.m)                     # sum of budgets = value of unit supplies at sum p = m
+    c = certify.certificate(mk.row_ptr, mk.col, mk.val, E @ r["p"], mk.m, r["x"], r["p"])
+    assert c["clearing"] < 1e-7 and c["bang_per_buck"] < 1e-7
