@@ -225,6 +225,7 @@ if torch is not None:
             out = solver.fisher_solve(row_ptr, col, val, w, m, tol=tol, precision=precision)
             ctx.solver = solver
             ctx.n = w.shape[0]
+            ctx.m = int(m)
             ctx.nnz = val.shape[0]
             ctx.val_dtype = val.dtype
             return out.p, out.util
@@ -234,7 +235,7 @@ if torch is not None:
             gp = grad_p.contiguous() if grad_p is not None else None
             gu = grad_util.contiguous() if grad_util is not None else None
             if gp is None:
-                gp = torch.zeros_like(gu[:1]).new_zeros(0)
+                gp = torch.zeros(ctx.m, dtype=torch.float64, device=gu.device if gu is not None else "cpu")
             grad_u, grad_w = ctx.solver.backward(gp, gu, nnz=ctx.nnz, n=ctx.n)
             ctx.solver.close()
             return grad_u.to(ctx.val_dtype), grad_w, None, None, None, None, None

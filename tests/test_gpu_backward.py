@@ -115,3 +115,44 @@ def test_autograd_function(solver):
     gu_o, gw_o, _ = A.fisher_backward(mk.row_ptr, mk.col, mk.val, mk.w, ref.x, ref.p, ref.t, r.cpu().numpy())
     assert np.max(np.abs(val.grad.cpu().numpy() - gu_o)) <= 1e-5 * np.max(np.abs(gu_o))
     assert np.max(np.abs(w.grad.cpu().numpy() - gw_o)) <= 1e-5 * np.max(np.abs(gw_o))
+
+
+def test_autograd_function_utilities_only_loss(solver):
+    """A loss that depends on the utilities t alone: the price gradient passed
+    to pdhcg_fisher_backward is zero (r = 0, g != 0), checked against the
+    oracle adjoint with the same seeds."""
+    torch = torch_cuda()
+    from paper_2506_06258_gb300.api import FisherEquilibrium
+    mk = S.bernoulli_market(30, 12, 0.4, seed=804)
+    val = torch.tensor(mk.val, device="cuda", requires_grad=True)
+    w = torch.tensor(mk.w, device="cuda", requires_grad=True)
+    _, t = FisherEquilibrium.apply(val, w, dev(mk.row_ptr), dev(mk.col), mk.m, 1e-11, "fp64")
+    g = torch.tensor(np.random.default_rng(4).normal(size=mk.n), device="cuda")
+    (g * t).sum().backward()
+    ref = F.pdhcg_solve(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, F.Params(tol=1e-13, max_iter=500000))
+    gu_o, gw_o, _ = A.fisher_backward(mk.row_ptr, mk.col, mk.val, mk.w, ref.x, ref.p, ref.t, np.zeros(mk.m),
+                                      g.cpu().numpy())
+    assert np.max(np.abs(gu_o)) > 0
+    assert np.max(np.abs(val.grad.cpu().numpy() - gu_o)) <= 1e-5 * np.max(np.abs(gu_o))
+    assert np.max(np.abs(w.grad.cpu().numpy() - gw_o)) <= 1e-5 * np.max(np.abs(gw_o))
+
+
+def test_backward_without_price_gradient_direct(solver):
+    """FisherEquilibrium.backward with grad_p None (autograd may pass None when
+    materialisation is off): it must build a zero price gradient of length m."""
+    torch = torch_cuda()
+    from paper_2506_06258_gb300.api import FisherEquilibrium, Solver
+    mk = S.bernoulli_market(20, 9, 0.4, seed=805)
+
+    class Ctx:
+        pass
+    ctx = Ctx()
+    val = dev(mk.val)
+    p, t = FisherEquilibrium.forward(ctx, val, dev(mk.w), dev(mk.row_ptr), dev(mk.col), mk.m, 1e-11, "fp64")
+    g = torch.ones(mk.n, dtype=torch.float64, device="cuda")
+    gu, gw, *_ = FisherEquilibrium.backward(ctx, None, g)
+    ref = F.pdhcg_solve(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, F.Params(tol=1e-13, max_iter=500000))
+    gu_o, gw_o, _ = A.fisher_backward(mk.row_ptr, mk.col, mk.val, mk.w, ref.x, ref.p, ref.t, np.zeros(mk.m),
+                                      np.ones(mk.n))
+    assert np.max(np.abs(host(gu) - gu_o)) <= 1e-5 * max(np.max(np.abs(gu_o)), 1e-12)
+    assert np.max(np.abs(host(gw) - gw_o)) <= 1e-5 * np.max(np.abs(gw_o))
