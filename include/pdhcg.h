@@ -248,25 +248,30 @@ pdhcg_status pdhcg_row_prox(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precis
 pdhcg_status pdhcg_kkt(pdhcg_handle h, const pdhcg_market* mk, pdhcg_precision prec,
                        const void* x, const double* p, double* out);
 
-/* pdhcg_kkt_noalloc: the same residuals as pdhcg_kkt for the FP64 value type,
- * for callers that cannot allocate device memory when they need them (code
- * running inside an allocator or memory-pool callback, a process whose device
- * memory is fully reserved by another framework, a real-time loop that forbids
- * allocation after start-up).  The paper has no counterpart; it is a
- * deployment variant of the Section 5 residual.
- *   mk, x[nnz] (double), p[m] (double): DEVICE pointers only, caller order,
- *   the caller's CSR (no preprocessing beyond the row scaling of Section 5);
+/* pdhcg_kkt_noalloc: the same three residuals as pdhcg_kkt, for callers that
+ * cannot allocate device memory at the moment they need them: code running
+ * inside an allocator or memory-pool callback (allocating there re-enters the
+ * allocator), a process whose device memory another framework has reserved in
+ * full, or a real-time loop that forbids allocation after start-up.  The paper
+ * has no counterpart to this entry point.
+ *   mk: DEVICE pointers only, the caller's CSR and row order; val may be
+ *       FP64 or FP32 (val_type), scaled per row by its maximum as pdhcg_kkt
+ *       does; every row must hold at least one entry.
+ *   x[nnz] (double), p[m] (double): DEVICE pointers, caller order.
  *   out[4]: host or device; r_primal, r_dual, r_gap, max of the three.
- *   stream: cudaStream_t as void* (0 = legacy default stream); synchronous.
+ *   stream: cudaStream_t as void* (0 = legacy default stream).
+ * The call is synchronous (it ends with a copy to the host and a stream
+ * synchronisation), so it must not be issued on a stream that is being
+ * captured into a CUDA graph; it returns PDHCG_ERR_INVALID on such a stream.
  * No call allocates: all scratch lives in one file-scope device array sized
  * for at most 262144 goods (about 4 MiB, held by every device that loads the
- * library until the process exits); larger m returns PDHCG_ERR_INVALID, as do
- * host input pointers and out-of-range indices (checked in the kernel).  The
- * first call made with a given device current looks the array's device address
- * up (cudaGetSymbolAddress); make that first call before any stream capture.
- * The array is shared by every call: each call clears what must start at zero,
- * and calls that overlap on the GPU (other streams or host threads) race, so
- * callers must serialise them. */
+ * library until the process exits).  PDHCG_ERR_INVALID is returned for larger
+ * m, host input pointers, an empty row, and out-of-range row pointers or
+ * column indices (checked in the kernel, which skips the bad entry).  The
+ * first call made with a given device current looks the array's device
+ * address up (cudaGetSymbolAddress).  The array is shared by every call: each
+ * call clears what must start at zero, and calls that overlap on the GPU
+ * (other streams or host threads) race, so callers must serialise them. */
 pdhcg_status pdhcg_kkt_noalloc(const pdhcg_market* mk, const double* x, const double* p, double* out,
                                void* stream);
 

@@ -56,6 +56,9 @@ __global__ void na_clear_kernel(NaScratch* S, int m) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         S->ctl.ticket = 0u;
         S->ctl.error = 0u;
+        // NaN until the goods pass writes the result: a pass that never ran
+        // cannot be mistaken for a converged point
+        for (int k = 0; k < 4; k++) S->ctl.out[k] = __longlong_as_double(0x7ff8000000000000ll);
     }
 }
 
@@ -235,17 +238,28 @@ pdhcg_status pdhcg_kkt_noalloc(const pdhcg_market* mk, const double* x, const do
     NaScratch* S = na_scratch_for_current_device(&err);
     if (!S) return PDHCG_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    // every call ends with a blocking copy and a stream synchronisation, which a
+    // capturing stream does not allow
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return PDHCG_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return PDHCG_ERR_INVALID;
     const int m = mk->m, n = mk->n;
     na_clear_kernel<<<(m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024, 256, 0, s>>>(S, m);
     na_rows_kernel<<<kNaRowBlocks, kNaThreads, 0, s>>>(n, m, mk->nnz, (const long long*)mk->row_ptr, mk->col,
                                                        mk->val, mk->val_type == PDHCG_VAL_F32 ? 1 : 0, mk->w, x,
                                                        p, S);
     na_goods_kernel<<<kNaGoodBlocks, kNaThreads, 0, s>>>(m, p, S);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return PDHCG_ERR_CUDA;
     NaCtl ctl;
     err = cudaMemcpyAsync(&ctl, &S->ctl, sizeof(NaCtl), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return PDHCG_ERR_CUDA;
     if (ctl.error) return PDHCG_ERR_INVALID;
+    if (ctl.out[3] != ctl.out[3]) return PDHCG_ERR_CUDA;     // the goods pass did not run
     if (is_device(out)) {
         err = cudaMemcpyAsync(out, S->ctl.out, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
