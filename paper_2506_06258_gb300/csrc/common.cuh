@@ -173,6 +173,42 @@ __device__ __forceinline__ float sr_add(float a, float b, unsigned r) {
 }
 
 
+// Cheaper generator for the row kernel: one full mix per (row, pass) and a
+// short xorshift-multiply per entry of the row (position k within the row),
+// in the manner of a Weyl sequence fed through a one-multiply finaliser.
+__device__ __forceinline__ unsigned row_hash(long long row, unsigned seed) {
+    return mix32((unsigned)row * 0x9E3779B1u ^ seed);
+}
+__device__ __forceinline__ unsigned entry_hash(unsigned rh, unsigned k) {
+    unsigned h = rh + k * 0x9E3779B9u;      // Weyl step by the golden-ratio constant
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    return h;
+}
+// uniform in [0, 1) from 23 random bits (the mantissa of a float in [1, 2))
+__device__ __forceinline__ float rand01_lo(unsigned bits) {
+    return __int_as_float(0x3f800000u | (bits & 0x7fffffu)) - 1.0f;
+}
+__device__ __forceinline__ float rand01_hi(unsigned bits) {
+    return __int_as_float(0x3f800000u | (bits >> 9)) - 1.0f;
+}
+// a + b (a, b such that the exact sum is >= 0) rounded stochastically with a
+// uniform r in [0, 1): s + e = a + b exactly (TwoSum); with h the spacing of
+// the floats next to s on the side of e, s + (e + r h) rounded DOWN is the
+// upper neighbour of the exact sum with probability equal to its distance from
+// the lower one over h, so the stored value is unbiased.  (At a power of two
+// the spacing below s is half the spacing above; taking h on e's side keeps
+// the probabilities exact there too.)
+__device__ __forceinline__ float sr_add_rd(float a, float b, float r) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const int sb = __float_as_int(s);
+    const float nb = __int_as_float(e >= 0.0f ? sb + 1 : sb - 1);
+    const float h = fabsf(nb - s);
+    return __fadd_rd(s, __fmaf_rn(r, h, e));
+}
 // a > b for normalised float-float values
 __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
@@ -275,6 +311,7 @@ struct DevMarket {
     const int* cj;
     const void* uv;        // float or double
     const double* w;
+    const float2* wff;     // MIXED: budgets as float-float (internal row order)
     Bucket buckets[kMaxBuckets];
     int nb;
     int hot;               // goods [0, hot) accumulate in shared memory
@@ -291,7 +328,8 @@ struct IterBufs {
     double* pbar;
     double* C[3];      // column sums c^{k-1}, c^k, c_new (roles in Ctl)
     unsigned long long* acc;   // fixed-point accumulators (MIXED) or double bits (FP64)
-    double* t;         // s* of the last pass (per row)
+    double* t;         // FP64: s* of the last pass (per row)
+    float2* yst;       // MIXED: y = w / s* of the last pass as float-float (per row)
     double* part;      // per-block partials of the row kernel
     double* part2;     // per-block partials of the dual kernel (2 per block)
     float2* pff_p;     // committed p and p-bar as float-float (for the MIXED KKT)

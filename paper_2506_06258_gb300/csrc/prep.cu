@@ -182,6 +182,40 @@ void k_entries(int n, const int* perm, const long long* crp, const long long* ir
     else
         entries_kernel<double><<<g, 256, 0, s>>>(n, perm, crp, irp, (const double*)src, (double*)dst, to_caller ? 1 : 0);
 }
+__global__ void w_to_ff_kernel(int n, const double* __restrict__ w, float2* __restrict__ wff) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = w[i];
+        const float h = (float)v;
+        wff[i] = make_float2(h, (float)(v - (double)h));
+    }
+}
+__global__ void t_to_y_kernel(int n, const double* __restrict__ w, const double* t, float2* y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double tv = t[i];
+        const double v = (tv > 0.0 && tv < 1e300) ? w[i] / tv : 1.0;
+        const float h = (float)v;
+        y[i] = make_float2(h, (float)(v - (double)h));
+    }
+}
+__global__ void y_to_t_kernel(int n, const double* __restrict__ w, const float2* y, double* t) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 v = y[i];
+        t[i] = w[i] / ((double)v.x + (double)v.y);
+    }
+}
+__global__ void fill_ff_kernel(int n, float2* a, float v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = make_float2(v, 0.0f);
+}
+void k_w_to_ff(int n, const double* w, float2* wff, cudaStream_t s) {
+    w_to_ff_kernel<<<grid_for(n), 256, 0, s>>>(n, w, wff);
+}
+void k_t_to_y(int n, const double* w, const double* t, float2* y, cudaStream_t s) {
+    t_to_y_kernel<<<grid_for(n), 256, 0, s>>>(n, w, t, y);
+}
+void k_y_to_t(int n, const double* w, const float2* y, double* t, cudaStream_t s) {
+    y_to_t_kernel<<<grid_for(n), 256, 0, s>>>(n, w, y, t);
+}
+void k_fill_ff(int n, float2* a, float v, cudaStream_t s) { fill_ff_kernel<<<grid_for(n), 256, 0, s>>>(n, a, v); }
 void k_fill(double* a, long long n, double v, cudaStream_t s) { fill_kernel<<<grid_for(n), 256, 0, s>>>(a, n, v); }
 void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, cudaStream_t s) {
     gather_goods_kernel<<<grid_for(m), 256, 0, s>>>(m, rank, src_int, dst);

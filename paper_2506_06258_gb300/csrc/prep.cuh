@@ -27,6 +27,13 @@ void k_gather_goods(int m, const int* rank, const double* src_int, double* dst, 
 void k_scatter_goods(int m, const int* rank, const double* src, double* dst_int, cudaStream_t s);
 void k_max_scaled_t(int n, const long long* rp, const float* uv, const double* t, double* out, cudaStream_t s);
 void k_convert(long long n, const void* src, bool src_f32, void* dst, bool dst_f32, cudaStream_t s);
+// MIXED row state: budgets as float-float, and y = w / t (the warm start of
+// the row kernel, float-float) from utilities t; y_to_t converts in place back
+// to t = w / y in FP64 (the two arrays may alias: same index, same 8 bytes).
+void k_w_to_ff(int n, const double* w, float2* wff, cudaStream_t s);
+void k_t_to_y(int n, const double* w, const double* t, float2* y, cudaStream_t s);
+void k_y_to_t(int n, const double* w, const float2* y, double* t, cudaStream_t s);
+void k_fill_ff(int n, float2* a, float v, cudaStream_t s);
 int dist_blocks();
 void k_dist_copy(bool f32, long long n, const void* a, void* r, double* part, cudaStream_t s);
 

@@ -17,6 +17,7 @@
 // remain in the oracle.
 #include "common.cuh"
 #include "rowsolve.cuh"
+#include "rowsolve_mixed.cuh"
 
 namespace pdhcg {
 
@@ -29,7 +30,7 @@ namespace pdhcg {
 template <int G>
 __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned long long* counter, const void* Xin,
                              void* Xout, const IterBufs& bf, const float2* sp, unsigned long long* acc_s,
-                             const RowCtx& rc, float& dxf, int& capped, int& evals) {
+                             const RowCtxM& rc, float& dxf, int& capped, int& evals) {
     constexpr int rpw = 32 / G;
     const int lane = threadIdx.x & 31;
     const long long units = (bk.count + rpw - 1) / rpw;
@@ -44,20 +45,20 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
         long long slot = (long long)base * rpw + lane / G;
         bool vn = slot < bk.count;
         int rn = vn ? (int)(bk.first + slot) : 0;
-        RowRegs nx;
-        row_load<G>(mk, U, Xi, rn, vn, nx);
+        RowRegsM nx;
+        rowm_load<G>(mk, U, Xi, rn, vn, nx);
         for (long long u = (long long)base; u < uend; u++) {
-            RowRegs cr = nx;
+            RowRegsM cr = nx;
             const int rc_row = rn;
             const bool vc = vn;
             if (u + 1 < uend) {
                 slot = (u + 1) * rpw + lane / G;
                 vn = slot < bk.count;
                 rn = vn ? (int)(bk.first + slot) : 0;
-                row_load<G>(mk, U, Xi, rn, vn, nx);
+                rowm_load<G>(mk, U, Xi, rn, vn, nx);
             }
-            row_mixed_core<G>(mk, U, Xi, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.t, rc,
-                                     rc_row, vc, dxf, capped, evals, cr);
+            rowm_core<G>(mk, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.yst, rc, rc_row, vc, dxf,
+                         capped, evals, cr);
         }
     }
 }
@@ -76,6 +77,12 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     rc.fold_w = (float)rc.fold_wd;
     rc.cap = ctl->row_cap;
     rc.seed = mix32((unsigned)ctl->passes * 2u + 1u);
+    RowCtxM rm;
+    rm.tau = rc.tau_hi;
+    rm.fold_w = rc.fold_w;
+    rm.fold = rc.fold;
+    rm.cap = rc.cap;
+    rm.seed = rc.seed;
     const int cur = ctl->cur;
     const void* Xin = fixed ? Xin_fixed : (cur ? bf.X[1] : bf.X[0]);
     void* Xout = fixed ? Xout_fixed : (cur ? bf.X[0] : bf.X[1]);
@@ -97,10 +104,10 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
         const int g = bk.g;
         if (MIXED && !bk.chunks) {
             switch (g) {
-                case 4: bucket_mixed<4>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
-                case 8: bucket_mixed<8>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
-                case 16: bucket_mixed<16>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
-                default: bucket_mixed<32>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rc, dxf, capped, evals); break;
+                case 4: bucket_mixed<4>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rm, dxf, capped, evals); break;
+                case 8: bucket_mixed<8>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rm, dxf, capped, evals); break;
+                case 16: bucket_mixed<16>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rm, dxf, capped, evals); break;
+                default: bucket_mixed<32>(mk, bk, &ctl->work[bi], Xin, Xout, bf, sp, acc_s, rm, dxf, capped, evals); break;
             }
             continue;
         }
@@ -118,8 +125,9 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
                 bool valid = slot < bk.count;
                 int row = valid ? (int)(bk.first + slot) : 0;
                 if (MIXED) {
-                    row_mixed_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff,
-                                   sp, acc_s, bf.acc, bf.t, rc, row, valid, dxf, capped, evals);
+                    if (valid)
+                        rowm_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff,
+                                  sp, acc_s, bf.acc, bf.yst, rm, row, dxf, capped, evals);
                 } else {
                     const double* U = (const double*)mk.uv;
                     double* Xo = (double*)Xout;
@@ -292,7 +300,7 @@ __global__ void flush_x_kernel(long long nnz, IterBufs bf, Ctl* ctl) {
         if (wgt == 1.0) {
             xb[i] = xv;
         } else {
-            if constexpr (sizeof(V) == sizeof(float)) xb[i] = sr_add(xb[i], wv * (xv - xb[i]), sr_bits(i, seed) >> 16);
+            if constexpr (sizeof(V) == sizeof(float)) xb[i] = sr_add_rd(xb[i], wv * (xv - xb[i]), rand01_hi(sr_bits(i, seed)));
             else xb[i] = xb[i] + wv * (xv - xb[i]);
         }
     }
@@ -427,6 +435,18 @@ void launch_to_ff(int m, const double* p, float2* pff, cudaStream_t s) {
     to_ff_kernel<<<vec_blocks(m), 256, 0, s>>>(m, p, pff);
 }
 
+// MIXED fixed pass: the y state starts at 1 (any y > 0 is a valid start) and
+// is converted to s = w / y afterwards, in place
+__global__ void yfill_kernel(int n, float2* y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = make_float2(1.0f, 0.0f);
+}
+__global__ void y_to_s_kernel(int n, const double* __restrict__ w, double* t) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 v = ((const float2*)t)[i];
+        t[i] = w[i] / ((double)v.x + (double)v.y);
+    }
+}
+
 void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* x_out, const double* p,
                        double tau, unsigned long long* acc, double* t_out, double* c_out,
                        double* part, Ctl* ctl, cudaStream_t s) {
@@ -434,14 +454,20 @@ void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* 
     IterBufs b = {};
     b.acc = acc;
     b.t = t_out;
+    b.yst = (float2*)t_out;     // MIXED: y state in the same buffer (8 bytes per row)
     b.part = part;
     // scratch for the converted prices lives after the m accumulators
     b.pff = (float2*)(acc + mk.m);
     b.pc = (double*)(acc + 2 * (size_t)mk.m);
     p_to_ff_kernel<<<vec_blocks(mk.m), 256, 0, s>>>(mk.m, p, b.pff, b.pc);
     ctl_fixed_kernel<<<1, 1, 0, s>>>(ctl, tau, 64);
-    if (mixed) prox_kernel<true><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
-    else prox_kernel<false><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
+    if (mixed) {
+        yfill_kernel<<<vec_blocks(mk.n), 256, 0, s>>>(mk.n, b.yst);
+        prox_kernel<true><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
+        y_to_s_kernel<<<vec_blocks(mk.n), 256, 0, s>>>(mk.n, mk.w, t_out);
+    } else {
+        prox_kernel<false><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
+    }
     cols_out_kernel<<<vec_blocks(mk.m), 256, 0, s>>>(mk.m, mixed, acc, c_out);
 }
 

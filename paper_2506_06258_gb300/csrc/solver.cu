@@ -241,6 +241,10 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     CK(cudaMemcpyAsync(h->inv.p, P.inv.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->rp.p, irp.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
     k_rows_to_internal(n, (const int*)h->perm.p, w, (double*)h->w.p, s);
+    if (mixed) {
+        CK(ensure(h->wff, (n + 2) * sizeof(float2)));
+        k_w_to_ff(n, (const double*)h->w.p, (float2*)h->wff.p, s);
+    }
     // scaled utilities, relabelled goods, initial x
     const size_t vb = mixed ? 4 : 8;
     CK(ensure(h->cj, (nnz + kPadEntries) * sizeof(int)));
@@ -257,6 +261,7 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
     D.cj = (const int*)h->cj.p;
     D.uv = h->uv.p;
     D.w = (const double*)h->w.p;
+    D.wff = mixed ? (const float2*)h->wff.p : nullptr;
     // hot goods in shared memory: as many as fit, but flushing them (blocks x
     // hot atomics) must stay small against nnz
     long long hot = std::min<long long>(m, mixed ? 4096 : 8192);
@@ -327,6 +332,7 @@ static IterBufs iter_bufs(pdhcg_handle h) {
     b.C[2] = (double*)h->C2.p;
     b.acc = (unsigned long long*)h->acc.p;
     b.t = (double*)h->t.p;
+    b.yst = h->prep.mixed ? (float2*)h->t.p : nullptr;   // MIXED keeps y = w / s in the same buffer
     b.part = (double*)h->part.p;
     b.part2 = (double*)h->part2.p;
     b.pff_p = h->prep.mixed ? (float2*)h->pff_p.p : nullptr;
@@ -347,6 +353,14 @@ static KktBufs kkt_bufs(pdhcg_handle h, double* c_out, double* t_out, int slot) 
     k.nd_part = (float*)h->ndpart.p;
     k.pff = slot == 0 ? (const float2*)h->pff_p.p : (const float2*)h->pff_pb.p;
     return k;
+}
+
+// Warm start of the row kernel from the utilities t_cur of the current point:
+// FP64 keeps s = t, MIXED keeps y = w / t as float-float.
+static void set_row_state(pdhcg_handle h, cudaStream_t s) {
+    const Prepared& P = h->prep;
+    if (P.mixed) k_t_to_y(P.n, (const double*)h->w.p, (const double*)h->t_cur.p, (float2*)h->t.p, s);
+    else cudaMemcpyAsync(h->t.p, h->t_cur.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
 }
 
 // restart test of Section 5 (PDLP/PDHCG adaptive restarts)
@@ -385,6 +399,9 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
     pdhcg_status st = alloc_iter(h);
     if (st != PDHCG_OK) return st;
     const double t0 = now_ms();
+    // budgets as float-float for the MIXED row kernel (the Arrow-Debreu loop
+    // changes h->w between solves)
+    if (mixed) k_w_to_ff(n, (const double*)h->w.p, (float2*)h->wff.p, s);
     const double sum_w = device_sum((const double*)h->w.p, n, h->part2, s);
     // initial point (reading: x_ij = 1/deg_j, p_j = sum(w)/m; omega_0 = ||p0||/||x0||)
     const double p_init = sum_w / m;
@@ -425,7 +442,7 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
     KktBufs kc = kkt_bufs(h, (double*)h->c_cur.p, (double*)h->t_cur.p, 0);
     launch_kkt(mixed, P.dm, h->X0.p, (const double*)h->p.p, kc, s);
     // utilities of the starting point: the row kernel's warm start y_0 = w / t
-    CK(cudaMemcpyAsync(h->t.p, h->t_cur.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    set_row_state(h, s);
     CK(cudaMemcpyAsync(h->C0.p, h->c_cur.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->C1.p, h->c_cur.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(&h->host->kout[0], h->kout.p, sizeof(KktOut), cudaMemcpyDeviceToHost, s));
@@ -559,7 +576,7 @@ pdhcg_status session_step(pdhcg_handle h, long long chunks) {
             }
             CK(cudaMemcpyAsync(Cbuf[c.ck], csrc, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
             CK(cudaMemcpyAsync(Cbuf[c.ckm1], csrc, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            CK(cudaMemcpyAsync(h->t.p, h->t_cur.p, P.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            set_row_state(h, s);
             // distances to the previous restart point, then remember this one
             const int nb = dist_blocks();
             std::vector<double> pa(nb), pb(nb);

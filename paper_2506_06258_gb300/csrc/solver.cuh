@@ -113,7 +113,7 @@ struct pdhcg_handle_s {
     // staged caller inputs / outputs
     pdhcg::DevBuf in_rp, in_col, in_val, in_w, in_x0, in_p0, o_p, o_u, o_x;
     // market
-    pdhcg::DevBuf rp, urp, perm, inv, w, err, deg, degint, rank, cj, uv, rowmax, p0i;
+    pdhcg::DevBuf rp, urp, perm, inv, w, wff, err, deg, degint, rank, cj, uv, rowmax, p0i;
     // iterates
     pdhcg::DevBuf X0, X1, Xb, Xr;
     pdhcg::DevBuf p, pc, pff, pbar, prs, C0, C1, C2, c_cur, c_avg, M, acc, t, t_cur, t_avg;
@@ -134,7 +134,7 @@ struct pdhcg_handle_s {
 
     void release() {
         pdhcg::DevBuf* all[] = {&in_rp, &in_col, &in_val, &in_w, &in_x0, &in_p0, &o_p, &o_u, &o_x,
-                                &rp, &urp, &perm, &inv, &w, &err, &deg, &degint, &rank, &cj, &uv, &rowmax, &p0i,
+                                &rp, &urp, &perm, &inv, &w, &wff, &err, &deg, &degint, &rank, &cj, &uv, &rowmax, &p0i,
                                 &X0, &X1, &Xb, &Xr, &p, &pc, &pff, &pbar, &prs, &C0, &C1, &C2, &c_cur,
                                 &c_avg, &M, &acc, &t, &t_cur, &t_avg, &part, &part2, &kpart, &gpart, &ctl,
                                 &kout, &pff_p, &pff_pb, &ndpart, &ad_w, &ad_wn, &ad_p, &ad_e_rp, &ad_e_col, &ad_e_val};

@@ -59,8 +59,10 @@ def test_row_prox_parity(solver, prec, seed):
     else:
         assert np.allclose(sg, so, rtol=1e-6)
         assert np.all(np.abs(xg - xo) <= 2e-6 * rowmaxx[rows] + 1e-30)
-        # exact fixed-point column sums of the FP32 iterate
-        assert np.allclose(cg, F.column_sums(sc.col, xg, mk.m), rtol=1e-9, atol=1e-11)
+        # exact fixed-point column sums of the FP32 iterate (unit 2^-40, round
+        # to nearest even per entry; integer work, compared bit for bit)
+        q = np.rint(xg * 2.0 ** 40)
+        assert np.array_equal(cg * 2.0 ** 40, np.bincount(mk.col, weights=q, minlength=mk.m))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

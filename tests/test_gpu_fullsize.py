@@ -58,6 +58,10 @@ def test_row_prox_full_size_sampled_rows(c3):
         s_ref, x_ref = F.row_prox_exact_single(u, a, cc)
         assert abs(sg[i] - s_ref) <= 1e-6 * s_ref, i
         assert np.max(np.abs(xg[b:e] - x_ref)) <= 2e-6 * max(np.max(x_ref), 1e-30), i
-    # the returned column sums are the exact sums of the returned x
-    csum = np.bincount(mk.col, weights=xg.astype(np.float64), minlength=mk.m)
-    assert np.allclose(cg, csum, rtol=1e-9, atol=1e-12)
+    # the returned column sums are the exact 64-bit fixed-point sums (unit
+    # 2^-40, each x rounded to the nearest unit, ties to even) of the returned
+    # x: integer work, so compared bit for bit.  Every rounded x and every
+    # partial sum is an integer below 2^53, so float64 sums them exactly.
+    q = np.rint(xg.astype(np.float64) * 2.0 ** 40)
+    csum_q = np.bincount(mk.col, weights=q, minlength=mk.m)
+    assert np.array_equal(cg * 2.0 ** 40, csum_q)
