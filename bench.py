@@ -11,9 +11,12 @@ average and the restart / termination decision.  Inputs are resident in HBM
 before the timed region; every pass streams ~24 GB, far above the 129 MB L2.
 
 Also reported on the same JSON line:
-  roofline      the row kernel's algorithmic bytes per launch (24 B x nnz) over
-                its average launch time, measured with CUDA events recorded
-                inside the iteration graph during the timed steps
+  roofline      the row kernel's algorithmic bytes per launch (16 B x nnz: u,
+                good id and x^k read, x^{k+1} written) over its average launch
+                time, measured with CUDA events recorded inside the iteration
+                graph during the timed steps; beside it the whole iteration
+                (24 B x nnz: the row pass plus the x-bar fold, which streams
+                16 B per entry every other iteration) over the timed step
   e2e           the same metric through pdhcg_fisher_solve with HOST buffers
                 (pinned), host<->device copies and preprocessing included
   cpu_baseline  the FP64 CPU oracle (as it stands) on a bounded row sample of
@@ -543,7 +546,8 @@ def main():
     prox_ms = info.prox_ms - info0.prox_ms
     launches = info.kernel_launches - info0.kernel_launches
     avg_prox_s = prox_ms * 1e-3 / max(prox_launches, 1)
-    alg_bytes = 24.0 * mk.nnz
+    alg_bytes = 16.0 * mk.nnz                  # the row kernel: u, good id, x^k read; x^{k+1} written
+    iter_bytes = 24.0 * mk.nnz                 # + the x-bar fold: 16 B per entry every other iteration
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / avg_prox_s / 1e9
     kkt_now = info.kkt
@@ -597,10 +601,13 @@ def main():
                    "kkt_after_timed_steps": kkt_now, "row_equation_evals_per_row_pass": round(evals_per_row, 3),
                    "l2": "inputs (24 GB/pass) far above L2 (129 MB)",
                    "generate_s": round(t_gen, 1)},
-        "roofline": {"bound": "hbm", "kernel": "prox_kernel (row subproblems + column sums + averaging)",
+        "roofline": {"bound": "hbm", "kernel": "prox_kernel (row subproblems + column sums)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                     "avg_launch_ms": avg_prox_s * 1e3, "launches_timed": prox_launches},
+                     "avg_launch_ms": avg_prox_s * 1e3, "launches_timed": prox_launches,
+                     "iteration": {"alg_bytes": iter_bytes, "ms": ms / max(iters, 1),
+                                   "achieved": iter_bytes / (ms * 1e-3 / max(iters, 1)) / 1e9,
+                                   "frac": iter_bytes / (ms * 1e-3 / max(iters, 1)) / 1e9 / peak}},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

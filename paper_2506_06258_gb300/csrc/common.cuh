@@ -58,6 +58,14 @@ struct Ctl {
     unsigned int ticket2;  // last-block-done counter of the KKT goods kernel
     int row_cap;           // active-set rounds per row solve
     int pad;
+    // MIXED x-bar folds in pairs: accepted iterates waiting to be folded (0, 1
+    // or 2; with 2 the older one is in X[1 - cur], the newer in X[cur]) and
+    // their weights eta_k / sum eta
+    double xf_w1, xf_w2;
+    int xf_n;
+    int xf_folded;         // the waiting pair has been folded (set by the fold kernel's last block)
+    unsigned int xf_ticket;   // last-block-done counter of the fold kernel
+    int pad2;
     unsigned long long work[kMaxBuckets];   // dynamic work counters of the row kernel
 };
 
@@ -343,6 +351,8 @@ void launch_prox(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, c
 void launch_dual(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
 void launch_to_ff(int m, const double* p, float2* pff, cudaStream_t s);
 void launch_flush(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
+// MIXED: fold two waiting accepted iterates into x-bar (no-op otherwise)
+void launch_fold(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s);
 // one standalone prox pass with fixed tau and prices (no step control)
 void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* x_out, const double* p,
                        double tau, unsigned long long* acc, double* t_out, double* c_out,

@@ -57,8 +57,8 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
                 rn = vn ? (int)(bk.first + slot) : 0;
                 rowm_load<G>(mk, U, Xi, rn, vn, nx);
             }
-            rowm_core<G>(mk, (float*)Xout, (float*)bf.Xb, bf.pff, sp, acc_s, bf.acc, bf.yst, rc, rc_row, vc, dxf,
-                         capped, evals, cr);
+            rowm_core<G>(mk, (float*)Xout, bf.pff, sp, acc_s, bf.acc, bf.yst, rc, rc_row, vc, dxf, capped, evals,
+                         cr);
         }
     }
 }
@@ -77,10 +77,8 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     rc.fold_w = (float)rc.fold_wd;
     rc.cap = ctl->row_cap;
     rc.seed = mix32((unsigned)ctl->passes * 2u + 1u);
-    RowCtxM rm;
+    RowCtxM rm;       // MIXED: x-bar is folded by fold_pair_kernel, not here
     rm.tau = rc.tau_hi;
-    rm.fold_w = rc.fold_w;
-    rm.fold = rc.fold;
     rm.cap = rc.cap;
     rm.seed = rc.seed;
     const int cur = ctl->cur;
@@ -126,8 +124,8 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
                 int row = valid ? (int)(bk.first + slot) : 0;
                 if (MIXED) {
                     if (valid)
-                        rowm_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, (float*)bf.Xb, bf.pff,
-                                  sp, acc_s, bf.acc, bf.yst, rm, row, dxf, capped, evals);
+                        rowm_long(mk, (const float*)mk.uv, (const float*)Xin, (float*)Xout, bf.pff, sp, acc_s,
+                                  bf.acc, bf.yst, rm, row, dxf, capped, evals);
                 } else {
                     const double* U = (const double*)mk.uv;
                     double* Xo = (double*)Xout;
@@ -261,11 +259,18 @@ __global__ void dual_kernel(DevMarket mk, IterBufs bf, Ctl* ctl, int nprox) {
     double eta_next = isinf(eta_max) ? grow : fmin((1.0 - pow(k1, -0.3)) * eta_max, grow);
     eta_next = fmin(fmax(eta_next, ctl->eta_min), ctl->eta_max_abs);
     const bool accept = (eta <= eta_max) || (eta <= ctl->eta_min * (1.0 + 1e-12));
+    // MIXED x-bar: a pair waiting at the start of this pass has been folded by
+    // the fold kernel that ran after the previous pass
+    int xf = ctl->xf_n == 2 ? 0 : ctl->xf_n;
+    ctl->xf_folded = 0;
     if (accept) {
         ctl->iters += 1;
         ctl->chunk_acc += 1;
         ctl->sum_eta += eta;
         ctl->fold_wgt = eta / ctl->sum_eta;
+        if (xf == 0) ctl->xf_w1 = ctl->fold_wgt;
+        else ctl->xf_w2 = ctl->fold_wgt;
+        xf++;
         ctl->eta_used = eta;
         ctl->fold_pending = 1;
         ctl->accepted = 1;
@@ -279,6 +284,7 @@ __global__ void dual_kernel(DevMarket mk, IterBufs bf, Ctl* ctl, int nprox) {
         ctl->fold_pending = 0;
         ctl->accepted = 0;
     }
+    ctl->xf_n = xf;
     ctl->eta = eta_next;
     ctl->tau = eta_next / om;
     ctl->sigma = eta_next * om;
@@ -289,22 +295,94 @@ __global__ void dual_kernel(DevMarket mk, IterBufs bf, Ctl* ctl, int nprox) {
 // ---------------------------------------------------------------------------
 template <typename V>
 __global__ void flush_x_kernel(long long nnz, IterBufs bf, Ctl* ctl) {
-    if (!ctl->fold_pending) return;
     const V* x = (const V*)(ctl->cur ? bf.X[1] : bf.X[0]);
     V* xb = (V*)bf.Xb;
-    const double wgt = ctl->fold_wgt;
-    const V wv = (V)wgt;
-    const unsigned seed = mix32((unsigned)ctl->passes * 2u + 2u);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz; i += (long long)gridDim.x * blockDim.x) {
-        V xv = x[i];
-        if (wgt == 1.0) {
-            xb[i] = xv;
-        } else {
-            if constexpr (sizeof(V) == sizeof(float)) xb[i] = sr_add_rd(xb[i], wv * (xv - xb[i]), rand01_hi(sr_bits(i, seed)));
-            else xb[i] = xb[i] + wv * (xv - xb[i]);
+    if constexpr (sizeof(V) == sizeof(float)) {
+        // MIXED: fold a single waiting accepted iterate (a pair has already
+        // been folded by fold_pair_kernel)
+        const int nf = ctl->xf_n;
+        if (nf != 1) return;
+        const V* xo = (const V*)(ctl->cur ? bf.X[0] : bf.X[1]);      // the older one of a pair
+        const double w1 = ctl->xf_w1, w2 = ctl->xf_w2;
+        const float fw1 = (float)w1, fw2 = (float)w2, c1 = (float)((1.0 - w2) * w1);
+        const unsigned seed = mix32((unsigned)ctl->passes * 2u + 2u);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz; i += (long long)gridDim.x * blockDim.x) {
+            const float r = rand01_hi(sr_bits(i, seed));
+            const float b = x[i];
+            float v;
+            if (nf == 1) v = (w1 == 1.0) ? b : sr_add_rd(xb[i], fw1 * (b - xb[i]), r);
+            else {
+                const float a = xo[i];
+                v = (w1 == 1.0) ? sr_add_rd(a, fw2 * (b - a), r) : sr_add_rd(xb[i], fmaf(c1, a - xb[i], fw2 * (b - xb[i])), r);
+            }
+            xb[i] = v;
+        }
+    } else {
+        if (!ctl->fold_pending) return;
+        const double wgt = ctl->fold_wgt;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz; i += (long long)gridDim.x * blockDim.x) {
+            const V xv = x[i];
+            xb[i] = (wgt == 1.0) ? xv : xb[i] + (V)wgt * (xv - xb[i]);
         }
     }
 }
+// MIXED x-bar, two accepted iterates at a time (Alg. 2 average, weights
+// eta_k / sum eta, reading R5).  Runs after every dual kernel and acts when two
+// accepted iterates are waiting: the older (weight w1) in X[1 - cur], the newer
+// (weight w2) in X[cur], both untouched until the next row pass writes
+// X[1 - cur].  Folding x_a then x_b,
+//     x-bar <- (1 - w2)(1 - w1) x-bar + (1 - w2) w1 x_a + w2 x_b
+//            = x-bar + c1 (x_a - x-bar) + w2 (x_b - x-bar),   c1 = (1 - w2) w1,
+// and w1 = 1 (the first iterate after a restart) gives x_a + w2 (x_b - x_a).
+// A streaming pass (16 B per entry for two iterations) instead of a fold
+// inside the row kernel, where its loads and registers slowed the row solve.
+__global__ void __launch_bounds__(256) fold_pair_kernel(long long nnz, IterBufs bf, Ctl* ctl) {
+    // the kernel runs after every dual kernel of the chunk graph, also after the
+    // idle ones at the end of a chunk: each pair is folded exactly once
+    if (ctl->xf_n != 2 || ctl->xf_folded) return;
+    const int cur = ctl->cur;
+    const float* __restrict__ xa = (const float*)(cur ? bf.X[0] : bf.X[1]);
+    const float* __restrict__ xn = (const float*)(cur ? bf.X[1] : bf.X[0]);
+    float* __restrict__ xb = (float*)bf.Xb;
+    const double w1 = ctl->xf_w1, w2 = ctl->xf_w2;
+    const bool first = w1 == 1.0;
+    const float fw2 = (float)w2, c1 = (float)((1.0 - w2) * w1);
+    const unsigned seed = mix32((unsigned)ctl->passes * 2u + 2u);
+    const long long n4 = nnz >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const float4 a = __ldcs((const float4*)xa + q);
+        const float4 b = __ldcs((const float4*)xn + q);
+        const float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcs((const float4*)xb + q);
+        const unsigned h = row_hash(q, seed);
+        float4 o;
+        o.x = first ? sr_add_rd(a.x, fw2 * (b.x - a.x), rand01_lo(entry_hash(h, 0)))
+                    : sr_add_rd(v.x, fmaf(c1, a.x - v.x, fw2 * (b.x - v.x)), rand01_lo(entry_hash(h, 0)));
+        o.y = first ? sr_add_rd(a.y, fw2 * (b.y - a.y), rand01_lo(entry_hash(h, 1)))
+                    : sr_add_rd(v.y, fmaf(c1, a.y - v.y, fw2 * (b.y - v.y)), rand01_lo(entry_hash(h, 1)));
+        o.z = first ? sr_add_rd(a.z, fw2 * (b.z - a.z), rand01_lo(entry_hash(h, 2)))
+                    : sr_add_rd(v.z, fmaf(c1, a.z - v.z, fw2 * (b.z - v.z)), rand01_lo(entry_hash(h, 2)));
+        o.w = first ? sr_add_rd(a.w, fw2 * (b.w - a.w), rand01_lo(entry_hash(h, 3)))
+                    : sr_add_rd(v.w, fmaf(c1, a.w - v.w, fw2 * (b.w - v.w)), rand01_lo(entry_hash(h, 3)));
+        __stcs((float4*)xb + q, o);
+    }
+    // the ragged tail (nnz not a multiple of 4)
+    for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz; i += stride) {
+        const float a = xa[i], b = xn[i];
+        const float r = rand01_lo(entry_hash(row_hash(i >> 2, seed), (unsigned)(i & 3)));
+        xb[i] = first ? sr_add_rd(a, fw2 * (b - a), r) : sr_add_rd(xb[i], fmaf(c1, a - xb[i], fw2 * (b - xb[i])), r);
+    }
+    // last block done: mark the pair folded (every block has read the flag by now)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->xf_ticket, 1u) == gridDim.x - 1) {
+            ctl->xf_ticket = 0u;
+            ctl->xf_folded = 1;
+        }
+    }
+}
+
 __global__ void flush_p_kernel(int m, IterBufs bf, Ctl* ctl) {
     const bool pending = ctl->fold_pending;
     const double wgt = ctl->fold_wgt;
@@ -324,7 +402,11 @@ __global__ void flush_p_kernel(int m, IterBufs bf, Ctl* ctl) {
         }
     }
 }
-__global__ void flush_done_kernel(Ctl* ctl) { ctl->fold_pending = 0; }
+__global__ void flush_done_kernel(Ctl* ctl) {
+    ctl->fold_pending = 0;
+    ctl->xf_n = 0;
+    ctl->xf_folded = 0;
+}
 
 // ---------------------------------------------------------------------------
 // launchers
@@ -386,6 +468,10 @@ void launch_dual(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, c
     if (mixed) dual_kernel<true><<<nb, 256, 0, s>>>(mk, b, ctl, mk.nprox);
     else dual_kernel<false><<<nb, 256, 0, s>>>(mk, b, ctl, mk.nprox);
 }
+void launch_fold(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s) {
+    if (!mixed) return;          // FP64 folds x-bar inside the row kernel, one iterate per pass
+    fold_pair_kernel<<<sm_count() * 8, 256, 0, s>>>(mk.nnz, b, ctl);
+}
 void launch_flush(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s) {
     int nbx = (int)((mk.nnz + 255) / 256);
     if (nbx > 4096) nbx = 4096;
@@ -425,6 +511,7 @@ __global__ void ctl_fixed_kernel(Ctl* ctl, double tau, int cap) {
     ctl->active = 1;
     ctl->tau = tau;
     ctl->fold_pending = 0;
+    ctl->xf_n = 0;
     ctl->cur = 0;
     ctl->row_cap = cap;
     ctl->capped = 0;

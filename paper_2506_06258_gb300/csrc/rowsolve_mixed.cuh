@@ -42,8 +42,6 @@ constexpr float kYMax = 1e30f;
 
 struct RowCtxM {
     float tau;
-    float fold_w;
-    bool fold;
     int cap;
     unsigned seed;      // pass counter mixed into the stochastic-rounding bits
 };
@@ -114,8 +112,7 @@ __device__ __forceinline__ void rowm_acc(unsigned long long* s, unsigned long lo
 // register-resident rows: G lanes per row, d <= G * kSlots
 // ---------------------------------------------------------------------------
 template <int G>
-__device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, float* __restrict__ Xb,
-                          const float2* __restrict__ pff, const float2* sp, unsigned long long* acc_s,
+__device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, const float2* __restrict__ pff, const float2* sp, unsigned long long* acc_s,
                           unsigned long long* acc_g, float2* __restrict__ yst, const RowCtxM& rc, int row, bool valid,
                           float& dx2, int& capped, int& evals, RowRegsM& R) {
     const int tl = (threadIdx.x & 31) & (G - 1);
@@ -260,9 +257,8 @@ __device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, float* 
         evals += nev;
     }
 
-    // ---- new iterate at the final y, average fold, column sums ----
+    // ---- new iterate at the final y, column sums ----
     const unsigned rh = row_hash(row, rc.seed);
-    const float fw = rc.fold_w;
 #pragma unroll
     for (int k = 0; k < kSlots; k++) {
         if (rj[k] < 0) continue;
@@ -274,10 +270,6 @@ __device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, float* 
         __stcs(Xout + idx, xn);
         const float d = xn - rx[k];
         dx2 = fmaf(d, d, dx2);
-        if (rc.fold) {
-            const float xb = Xb[idx];
-            Xb[idx] = (fw == 1.0f) ? rx[k] : sr_add_rd(xb, fw * (rx[k] - xb), rand01_hi(hb));
-        }
         rowm_acc(acc_s, acc_g, mk.hot, rj[k], xn, false);
     }
 }
@@ -286,7 +278,6 @@ __device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, float* 
 // rows longer than 32 * kSlots entries: one warp per row, the row streamed in
 // chunks of 32 * kSlots entries and re-read (from L2) on every sweep.  The
 // iteration and its stopping rule are those of rowm_core; what differs:
-//  - x-bar is folded during the first sweep (the fold needs x^k only);
 //  - the first activity check (after a frozen-model step) writes x^{k+1}, its
 //    column sums and ||dx||^2 at the new y behind the check.  When the counts
 //    are unchanged that y is final and no write sweep follows; otherwise the
@@ -297,7 +288,7 @@ __device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, float* 
 // Every lane of the warp calls this with the same row.
 // ---------------------------------------------------------------------------
 __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ U, const float* __restrict__ Xin,
-                                 float* __restrict__ Xout, float* __restrict__ Xb, const float2* __restrict__ pff,
+                                 float* __restrict__ Xout, const float2* __restrict__ pff,
                                  const float2* sp, unsigned long long* acc_s, unsigned long long* acc_g,
                                  float2* __restrict__ yst, const RowCtxM& rc, int row, float& dx2, int& capped,
                                  int& evals) {
@@ -358,9 +349,8 @@ __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ 
 
     // the row's arrays into L2 ahead of the chunk loads (one bulk prefetch per
     // array; 16-byte aligned window, the arrays carry slack after their end)
-    if (lane < 4 && (lane < 3 || rc.fold)) {
-        const char* base = lane == 0 ? (const char*)(mk.cj + b)
-                           : lane == 1 ? (const char*)(U + b) : lane == 2 ? (const char*)(Xin + b) : (const char*)(Xb + b);
+    if (lane < 3) {
+        const char* base = lane == 0 ? (const char*)(mk.cj + b) : lane == 1 ? (const char*)(U + b) : (const char*)(Xin + b);
         const unsigned long long a0 = (unsigned long long)base & ~15ull;
         const unsigned long long a1 = ((unsigned long long)base + (unsigned long long)(e - b) * 4ull + 15ull) & ~15ull;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0)) : "memory");
@@ -371,8 +361,7 @@ __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ 
     if (!(y0.x > 0.0f) || !isfinite(y0.x)) y0 = make_float2(1.0f, 0.0f);
     float yh = y0.x, yl = y0.y;
 
-    // ---- first sweep: s0, the evaluation at y_0, the x-bar fold ----
-    const float fw = rc.fold_w;
+    // ---- first sweep: s0 and the evaluation at y_0 ----
     float s0h = 0.0f, s0l = 0.0f, C = 0.0f, A = 0.0f, Q = 0.0f;
     int cnt = 0;
     for (int c = 0; c < nch; c++) {
@@ -391,11 +380,6 @@ __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ 
             if (td < x) {
                 Q = fmaf(u, u, Q);
                 cnt++;
-            }
-            if (rc.fold && rj[k] >= 0) {
-                const int pos = c * span + k * 32 + lane;
-                const float xb = Xb[b + pos];
-                Xb[b + pos] = (fw == 1.0f) ? x : sr_add_rd(xb, fw * (x - xb), rand01_hi(entry_hash(rh, (unsigned)pos)));
             }
         }
     }

@@ -468,6 +468,7 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
         launch_prox(mixed, P.dm, bf, ctl, s);
         if (timing) cudaEventRecordWithFlags(S.ev[2 * q + 1], s, cudaEventRecordExternal);
         launch_dual(mixed, P.dm, bf, ctl, s);
+        launch_fold(mixed, P.dm, bf, ctl, s);
     }
     launch_flush(mixed, P.dm, bf, ctl, s);
     if (timing) cudaEventRecordWithFlags(S.ev[2 * passes], s, cudaEventRecordExternal);
@@ -604,6 +605,8 @@ pdhcg_status session_step(pdhcg_handle h, long long chunks) {
             c.sum_eta = 0.0;
             c.fold_pending = 0;
             c.fold_wgt = 1.0;
+            c.xf_n = 0;
+            c.xf_folded = 0;
             CK(cudaMemcpyAsync(h->ctl.p, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
             S.kkt_rs = kc;
             S.kkt_prev = INFINITY;
