@@ -46,8 +46,12 @@ struct RowCtxM {
     unsigned seed;      // pass counter mixed into the stochastic-rounding bits
 };
 
+// A row's entries, G lanes per row: lane tl holds entries tl, tl + G, ...
+// Addresses are formed once per row (64-bit base + lane); the slots then
+// differ by compile-time offsets, and bounds are 32-bit.
 struct RowRegsM {
-    long long b, e;
+    long long b;        // first entry of the row
+    int d;              // entries in the row
     float u[kSlots], x[kSlots];
     int j[kSlots];
 };
@@ -56,15 +60,18 @@ template <int G>
 __device__ __forceinline__ void rowm_load(const DevMarket& mk, const float* __restrict__ U,
                                           const float* __restrict__ Xin, int row, bool valid, RowRegsM& R) {
     const int tl = (threadIdx.x & 31) & (G - 1);
-    R.b = valid ? mk.rp[row] : 0;
-    R.e = valid ? mk.rp[row + 1] : 0;
+    const long long b = valid ? mk.rp[row] : 0;
+    R.b = b;
+    R.d = valid ? (int)(mk.rp[row + 1] - b) : 0;
+    const int* __restrict__ cp = mk.cj + b + tl;
+    const float* __restrict__ up = U + b + tl;
+    const float* __restrict__ xp = Xin + b + tl;
 #pragma unroll
     for (int k = 0; k < kSlots; k++) {
-        const long long idx = R.b + k * G + tl;
-        if (idx < R.e) {
-            R.j[k] = __ldg(mk.cj + idx);
-            R.u[k] = __ldg(U + idx);
-            R.x[k] = __ldcs(Xin + idx);
+        if (k * G + tl < R.d) {
+            R.j[k] = __ldg(cp + k * G);
+            R.u[k] = __ldg(up + k * G);
+            R.x[k] = __ldcs(xp + k * G);
         } else {
             R.j[k] = -1;
             R.u[k] = 0.0f;
@@ -259,15 +266,15 @@ __device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, const f
 
     // ---- new iterate at the final y, column sums ----
     const unsigned rh = row_hash(row, rc.seed);
+    float* __restrict__ xo = Xout + R.b + tl;
 #pragma unroll
     for (int k = 0; k < kSlots; k++) {
         if (rj[k] < 0) continue;
-        const long long idx = R.b + k * G + tl;
         const unsigned hb = entry_hash(rh, (unsigned)(k * G + tl));
         const float td = rtd[k];
         // x^{k+1} = [x^k - tau d]_+, stochastically rounded
         const float xn = td < rx[k] ? sr_add_rd(rx[k], -td, rand01_lo(hb)) : 0.0f;
-        __stcs(Xout + idx, xn);
+        __stcs(xo + k * G, xn);
         const float d = xn - rx[k];
         dx2 = fmaf(d, d, dx2);
         rowm_acc(acc_s, acc_g, mk.hot, rj[k], xn, false);
@@ -296,20 +303,25 @@ __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ 
     constexpr int span = 32 * kSlots;
     const long long b = mk.rp[row];
     const long long e = mk.rp[row + 1];
-    const int nch = (int)((e - b + span - 1) / span);
+    const int dr = (int)(e - b);
+    const int nch = (dr + span - 1) / span;
+    const int* __restrict__ cjr = mk.cj + b + lane;      // this lane's entries: + c * span + k * 32
+    const float* __restrict__ ur = U + b + lane;
+    const float* __restrict__ xr = Xin + b + lane;
+    float* __restrict__ xw = Xout + b + lane;
     const float tau = rc.tau;
     const unsigned rh = row_hash(row, rc.seed);
 
     float ru[kSlots], rx[kSlots], rph[kSlots], rpl[kSlots], rtd[kSlots];
     int rj[kSlots];
     auto load_chunk = [&](int c) {
+        const int o = c * span;
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
-            const long long idx = b + (long long)c * span + k * 32 + lane;
-            if (idx < e) {
-                rj[k] = __ldg(mk.cj + idx);
-                ru[k] = __ldg(U + idx);
-                rx[k] = Xin[idx];
+            if (o + k * 32 + lane < dr) {
+                rj[k] = __ldg(cjr + o + k * 32);
+                ru[k] = __ldg(ur + o + k * 32);
+                rx[k] = xr[o + k * 32];
             } else {
                 rj[k] = -1; ru[k] = 0.0f; rx[k] = 0.0f;
             }
@@ -335,11 +347,11 @@ __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ 
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
             if (rj[k] < 0) continue;
-            const int pos = c * span + k * 32 + lane;
+            const int pos = c * span + k * 32;
             const float td = rtd[k];
-            const float xn = td < rx[k] ? sr_add_rd(rx[k], -td, rand01_lo(entry_hash(rh, (unsigned)pos))) : 0.0f;
+            const float xn = td < rx[k] ? sr_add_rd(rx[k], -td, rand01_lo(entry_hash(rh, (unsigned)(pos + lane)))) : 0.0f;
             if (!undo) {
-                __stcs(Xout + b + pos, xn);
+                __stcs(xw + pos, xn);
                 const float d = xn - rx[k];
                 dx2 = fmaf(d, d, dx2);
             }
