@@ -146,76 +146,183 @@ def profiled_traffic(nnz_timed):
         return None
 
 
-def cpu_baseline(cfg, seconds=20.0, seed_rows=None):
-    """The FP64 oracle as it stands: PDHCG iterations on a row sample of the
-    same workload shape (same m and degree law, n and nnz scaled down), for
-    about `seconds` of CPU time; iterations/s scaled to nnz = 1e9."""
-    from oracle import fisher as F
+# ---------------------------------------------------------------------------
+# the FP64 oracle as the CPU baseline and the reference arm
+# ---------------------------------------------------------------------------
+# One oracle PDHCG iteration = the price step (Eq. update:py), the exact row
+# subproblems of every buyer (Section 2.2) and the column sums, the oracle's
+# own functions called as they stand.  The rows are independent given the
+# prices, so the all-core timing splits them into contiguous blocks, one
+# spawned process per core, each calling oracle.fisher.primal_step on its
+# block; prices and column-sum parts travel through shared memory.
+
+def _oracle_sample(cfg, frac=1e-3):
     from paper_2506_06258_gb300 import synth as S
-    frac = 1e-3
     n = max(1000, int(cfg["n"] * frac))
-    nnz_t = max(100_000, int(cfg["nnz_target"] * frac))
-    mk = S.config3(n=n, m=cfg["m"], nnz_target=nnz_t, fp32=False)
-    sc = F.preprocess(mk.row_ptr, mk.col, mk.val, mk.w, mk.m)
-    x, p = F.initial_point(sc)
-    c = F.column_sums(sc.col, x, mk.m)
-    tau = sigma = 0.9 / np.sqrt(sc.deg_col.max())
-    it = 0
-    t0 = time.perf_counter()
-    cm1 = c.copy()
-    while time.perf_counter() - t0 < seconds or it < 2:
-        p_new = F.price_step(p, c, cm1, sigma)
-        x, _ = F.primal_step(sc, x, p_new, tau)
-        cm1, c = c, F.column_sums(sc.col, x, mk.m)
-        p = p_new
-        it += 1
-    dt = time.perf_counter() - t0
-    rate = it / dt * (mk.nnz / NNZ_UNIT)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{it} oracle PDHCG iterations (price step, exact row subproblems, column sums) on a "
-                      f"{n}-buyer, {mk.m}-good, {mk.nnz}-nnz market of the same law ({dt:.1f} s); "
-                      f"rate scaled by nnz/1e9"}
+    mk = S.config3(n=n, m=cfg["m"], nnz_target=max(100_000, int(cfg["nnz_target"] * frac)), fp32=False)
+    return mk
+
+
+def _oracle_worker(conn, shm_names, m, rp, col, val, w, x0, slot):
+    from multiprocessing import shared_memory
+    from oracle import fisher as F
+    sp = shared_memory.SharedMemory(name=shm_names[0])
+    sc_ = shared_memory.SharedMemory(name=shm_names[1])
+    p = np.ndarray((m,), dtype=np.float64, buffer=sp.buf)
+    parts = np.ndarray((shm_names[2], m), dtype=np.float64, buffer=sc_.buf)
+    sc = F.preprocess(rp, col, val, w, m)
+    x = x0.copy()
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        x, _ = F.primal_step(sc, x, p, msg)
+        parts[slot] = F.column_sums(sc.col, x, m)
+        conn.send(1)
+    del p, parts
+    sp.close()
+    sc_.close()
+
+
+class OracleIterations:
+    """Oracle PDHCG iterations on a market, on `cores` processes (1 = in process)."""
+
+    def __init__(self, mk, cores=1):
+        from oracle import fisher as F
+        self.F, self.mk, self.cores = F, mk, max(1, cores)
+        deg = np.bincount(mk.col, minlength=mk.m).astype(np.float64)
+        x0 = 1.0 / deg[mk.col]                                 # R10, with the market's column degrees
+        self.p = np.full(mk.m, mk.w.sum() / mk.m)
+        self.tau = self.sigma = 0.9 / np.sqrt(deg.max())
+        if self.cores == 1:
+            self.sc = F.preprocess(mk.row_ptr, mk.col, mk.val, mk.w, mk.m)
+            self.x = x0
+            self.c = F.column_sums(self.sc.col, self.x, mk.m)
+        else:
+            import multiprocessing as mp
+            from multiprocessing import shared_memory
+            ctx = mp.get_context("spawn")
+            for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                os.environ[var] = "1"          # one thread per worker process
+            self.shm_p = shared_memory.SharedMemory(create=True, size=8 * mk.m)
+            self.shm_c = shared_memory.SharedMemory(create=True, size=8 * mk.m * self.cores)
+            self.pv = np.ndarray((mk.m,), dtype=np.float64, buffer=self.shm_p.buf)
+            self.parts = np.ndarray((self.cores, mk.m), dtype=np.float64, buffer=self.shm_c.buf)
+            # contiguous row blocks of about equal nnz
+            cuts = np.searchsorted(mk.row_ptr, np.linspace(0, mk.nnz, self.cores + 1)[1:-1])
+            bounds = [0, *[int(c) for c in cuts], mk.n]
+            self.procs, self.conns = [], []
+            for k in range(self.cores):
+                r0, r1 = bounds[k], bounds[k + 1]
+                z0, z1 = int(mk.row_ptr[r0]), int(mk.row_ptr[r1])
+                a, b = ctx.Pipe()
+                pr = ctx.Process(target=_oracle_worker, daemon=True,
+                                 args=(b, (self.shm_p.name, self.shm_c.name, self.cores), mk.m,
+                                       mk.row_ptr[r0:r1 + 1] - z0, mk.col[z0:z1], mk.val[z0:z1], mk.w[r0:r1],
+                                       x0[z0:z1], k))
+                pr.start()
+                b.close()                      # the child's end: a dead child then reads as EOF here
+                self.procs.append(pr)
+                self.conns.append(a)
+            for a in self.conns:
+                self._recv(a, 600.0)
+            self.c = F.column_sums(mk.col, x0, mk.m)
+        self.cm1 = self.c.copy()
+
+    def _recv(self, a, timeout):
+        # bounded wait: a worker that died or stalls ends the baseline with an error
+        if not a.poll(timeout):
+            self.close(force=True)
+            raise RuntimeError("oracle worker did not answer")
+        return a.recv()
+
+    def step(self):
+        p_new = self.F.price_step(self.p, self.c, self.cm1, self.sigma)
+        if self.cores == 1:
+            self.x, _ = self.F.primal_step(self.sc, self.x, p_new, self.tau)
+            c_new = self.F.column_sums(self.sc.col, self.x, self.mk.m)
+        else:
+            self.pv[:] = p_new
+            for a in self.conns:
+                a.send(self.tau)
+            for a in self.conns:
+                self._recv(a, 600.0)
+            c_new = self.parts.sum(axis=0)
+        self.cm1, self.c, self.p = self.c, c_new, p_new
+
+    def close(self, force=False):
+        if self.cores > 1 and self.procs:
+            for a in self.conns:
+                try:
+                    a.send(None)
+                except (BrokenPipeError, OSError):
+                    pass
+            for pr in self.procs:
+                pr.join(timeout=5 if force else 30)
+                if pr.is_alive():
+                    pr.terminate()
+                    pr.join(timeout=5)
+            self.procs = []
+            del self.pv, self.parts
+            self.shm_p.close()
+            self.shm_p.unlink()
+            self.shm_c.close()
+            self.shm_c.unlink()
+
+
+def _time_oracle(mk, cores, seconds=None, steps=None, warmup=1):
+    it = OracleIterations(mk, cores)
+    try:
+        for _ in range(warmup):
+            it.step()
+        n = 0
+        t0 = time.perf_counter()
+        while (steps is not None and n < steps) or (steps is None and (time.perf_counter() - t0 < seconds or n < 2)):
+            it.step()
+            n += 1
+        dt = time.perf_counter() - t0
+    finally:
+        it.close()
+    return n, dt
+
+
+def cpu_baseline(cfg, seconds=20.0):
+    """The FP64 oracle as it stands, timed on a bounded row sample of the same
+    workload law (same m and degree law, n and nnz scaled by 1e-3) for about
+    `seconds` each: on one core, and on all host cores (os.cpu_count()
+    processes over row blocks).  Iterations/s scaled to nnz = 1e9."""
+    mk = _oracle_sample(cfg)
+    cores = os.cpu_count() or 1
+    n1, dt1 = _time_oracle(mk, 1, seconds=seconds)
+    na, dta = _time_oracle(mk, cores, seconds=seconds) if cores > 1 else (n1, dt1)
+    scale = mk.nnz / NNZ_UNIT
+    desc = (f"oracle PDHCG iterations (price step, exact row subproblems of every buyer, column sums) on a "
+            f"{mk.n}-buyer, {mk.m}-good, {mk.nnz}-nnz market of the same law; rate scaled by nnz/1e9")
+    return {"value": na / dta * scale, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{na} iterations on {cores} processes over row blocks ({dta:.1f} s); " + desc,
+            "single_core": {"value": n1 / dt1 * scale, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} iterations in one process ({dt1:.1f} s)"}}
 
 
 # ---------------------------------------------------------------------------
 def run_reference(args, cfg, rank):
     if rank != 0:
         return
-    from oracle import fisher as F
-    from paper_2506_06258_gb300 import synth as S
-    frac = 1e-3
-    n = max(1000, int(cfg["n"] * frac))
-    mk = S.config3(n=n, m=cfg["m"], nnz_target=max(100_000, int(cfg["nnz_target"] * frac)), fp32=False)
-    sc = F.preprocess(mk.row_ptr, mk.col, mk.val, mk.w, mk.m)
-    x, p = F.initial_point(sc)
-    c = F.column_sums(sc.col, x, mk.m)
-    cm1 = c.copy()
-    tau = sigma = 0.9 / np.sqrt(sc.deg_col.max())
-
-    def step():
-        nonlocal x, p, c, cm1
-        p_new = F.price_step(p, c, cm1, sigma)
-        x, _ = F.primal_step(sc, x, p_new, tau)
-        cm1, c = c, F.column_sums(sc.col, x, mk.m)
-        p = p_new
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    value = args.steps / dt * (mk.nnz / NNZ_UNIT)
-    sample = (f"each step = one oracle PDHCG iteration on a {n}-buyer, {mk.m}-good, {mk.nnz}-nnz row sample of "
-              f"the workload; rate scaled by nnz/1e9")
+    mk = _oracle_sample(cfg)
+    cores = os.cpu_count() or 1
+    n, dt = _time_oracle(mk, cores, steps=args.steps, warmup=args.warmup)
+    value = n / dt * (mk.nnz / NNZ_UNIT)
+    sample = (f"each step = one oracle PDHCG iteration (price step, exact row subproblems, column sums) on a "
+              f"{mk.n}-buyer, {mk.m}-good, {mk.nnz}-nnz row sample of the workload, {cores} processes over row "
+              f"blocks; rate scaled by nnz/1e9")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(n, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(cfg), "reference": "FP64 CPU oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
 
 
 # ---------------------------------------------------------------------------
@@ -450,6 +557,61 @@ def _study_sections(sol, S):
     return out
 
 
+def _gpu_iter_rate(solver, capi, torch, stream, rp, col, val, w, m, prec, nnz, warm=1, timed=1):
+    """Iterations/s of one precision on a device-resident market: `warm`
+    check periods untimed, then `timed` check periods between CUDA events."""
+    market = solver.market(rp, col, val, w, m)
+    prm = capi.default_params(tol=1e-6, prec=prec, timing=1)
+    st = capi.pdhcg_fisher_begin(solver.h, market, prm, None, None)
+    if st:
+        raise capi.PdhcgError(st, "pdhcg_fisher_begin")
+    i0, i1 = capi.pdhcg_info(), capi.pdhcg_info()
+    capi.pdhcg_fisher_step(solver.h, warm, i0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    capi.pdhcg_fisher_step(solver.h, timed, i1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = i1.iters - i0.iters
+    launches = max(i1.prox_launches - i0.prox_launches, 1)
+    row_ms = (i1.prox_ms - i0.prox_ms) / launches
+    capi.pdhcg_fisher_end(solver.h, None, None, None, None)
+    bpe = 44.0 if prec == capi.PDHCG_FP64 else 24.0
+    return {"iters_per_s": its / (ms * 1e-3) if ms > 0 else 0.0, "iters_timed": int(its), "ms": ms,
+            "row_kernel_ms": row_ms, "alg_bytes_per_iter": bpe * nnz,
+            "achieved_GB_per_s": bpe * nnz / (ms * 1e-3 / max(its, 1)) / 1e9}
+
+
+def _time_to_tol_c2(solver, capi, torch, stream, dev, S, limit_s):
+    """C2 (n = 1e6 buyers, m = 1e4 goods, 100 distinct uniform goods per buyer,
+    nnz = 1e8, LogNormal(0,1) utilities, w ~ U(0.5,1.5)): one MIXED solve to
+    relative KKT 1e-6 from device-resident inputs (validation, preprocessing and
+    the iteration loop timed), with the GPU's own Section 5 residuals of the
+    returned point; and FP64 iterations/s on the same market."""
+    mk = S.config2(fp32=True)
+    rp, col, w = (torch.from_numpy(a).to(dev) for a in (mk.row_ptr, mk.col, mk.w))
+    val = torch.from_numpy(mk.val).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = solver.fisher_solve(rp, col, val, w, mk.m, tol=1e-6, precision="mixed", check=False,
+                              time_limit_s=limit_s)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    i = out.info
+    res = {"workload": "C2: n=1e6, m=1e4, 100 distinct uniform goods per buyer (nnz=1e8), LogNormal(0,1), "
+                       "w~U(0.5,1.5), MIXED, relative KKT 1e-6", "nnz": int(mk.nnz), "seconds": dt,
+           "status": int(out.status), "converged": int(out.status) == 0, "iters": int(i["iters"]),
+           "restarts": int(i["restarts"]), "kkt": i["kkt"], "r_primal": i["r_primal"], "r_dual": i["r_dual"],
+           "r_gap": i["r_gap"], "setup_s": i["setup_ms"] * 1e-3, "loop_s": i["solve_ms"] * 1e-3}
+    val64 = torch.from_numpy(mk.val.astype(np.float64)).to(dev)
+    res["fp64_iters_per_s"] = _gpu_iter_rate(solver, capi, torch, stream, rp, col, val64, w, mk.m,
+                                             capi.PDHCG_FP64, mk.nnz)["iters_per_s"]
+    res["mixed_iters_per_s"] = i["iters"] / max(i["solve_ms"] * 1e-3, 1e-9)
+    return res
+
+
 def run_study(which):
     import torch
     import __graft_entry__ as g
@@ -475,7 +637,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--time-to-tol", action="store_true", help="also run one full solve to tol 1e-6")
+    ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false",
+                    help="skip the C2 solve to relative KKT 1e-6 (on by default)")
+    ap.add_argument("--ttt-limit-s", type=float, default=300.0, help="time cap of the time-to-tolerance solve")
+    ap.add_argument("--no-fp64-arm", dest="fp64_arm", action="store_false",
+                    help="skip the plain FP64 GPU iterations/s on the same workload (on by default)")
     ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad", "sections"], default=None,
                     help="instead of the bench line, run one comparison study and print its JSON line")
     args = ap.parse_args()
@@ -578,12 +744,22 @@ def main():
                "note": "each step = pdhcg_fisher_solve from pinned host buffers: upload, validation, "
                        "preprocessing, one 64-iteration check period, download of p and utilities"}
 
+    # ---- the plain FP64 GPU arm on the same workload (same-GPU comparison) ----
+    fp64 = None
+    if args.fp64_arm:
+        val64 = torch.from_numpy(mk.val.astype(np.float64)).to(dev)
+        fp64 = {"workload": "the same C3 market, FP64 values, iterates and reductions",
+                **_gpu_iter_rate(solver, capi, torch, stream, rp_d, col_d, val64, w_d, mk.m, capi.PDHCG_FP64, mk.nnz)}
+        fp64["mixed_speedup"] = value / world / fp64["iters_per_s"] if fp64["iters_per_s"] > 0 else None
+        del val64
+
+    # ---- time to relative KKT 1e-6 (C2: the C3 solve to 1e-6 does not fit a
+    # default run: its top good sits in about every row, so ||K||_2 ~ 3e3 caps
+    # the step size and the solve needs ~1e5+ iterations) ----
     ttt = None
-    if args.time_to_tol:
-        prm_t = capi.default_params(tol=1e-6, prec=capi.PDHCG_MIXED)
-        out = solver.fisher_solve(rp_d, col_d, val_d, w_d, mk.m, tol=1e-6, precision="mixed")
-        ttt = {"seconds": (out.info["solve_ms"] + out.info["setup_ms"]) * 1e-3, "iters": out.info["iters"],
-               "kkt": out.info["kkt"], "status": out.status}
+    if args.time_to_tol and rank == 0:
+        ttt = _time_to_tol_c2(solver, capi, torch, stream, dev, S, args.ttt_limit_s)
+    solver.close()
     solver.close()
 
     if rank != 0:
@@ -615,6 +791,8 @@ def main():
     }
     if ttt:
         line["time_to_tol"] = ttt
+    if fp64:
+        line["fp64_arm"] = fp64
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -22,3 +22,25 @@ def test_reference_arm_prints_a_complete_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_all_core_oracle_harness_matches_one_process():
+    """The all-core CPU baseline splits the buyers into row blocks, one spawned
+    process each; after a few iterations its prices and column sums equal those
+    of the oracle run in one process (the row subproblems are independent
+    given the prices, so only the summation order of the column sums differs)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2506_06258_gb300 import synth as S
+    mk = S.config3(n=2000, m=300, nnz_target=60_000, fp32=False)
+    one, two = bench.OracleIterations(mk, 1), bench.OracleIterations(mk, 3)
+    try:
+        for _ in range(4):
+            one.step()
+            two.step()
+        assert np.allclose(one.p, two.p, rtol=1e-12, atol=1e-14)
+        assert np.allclose(one.c, two.c, rtol=1e-12, atol=1e-14)
+    finally:
+        one.close()
+        two.close()
