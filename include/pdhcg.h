@@ -100,6 +100,14 @@ typedef struct {
     int32_t verbose;           /* 0 silent, 1 one line per check to stderr          */
     int32_t timing;            /* 1: time every row-kernel launch with CUDA events
                                   (fills pdhcg_info.prox_ms / prox_launches)        */
+    int32_t batch_lanes;       /* batched solves: lanes per row.  0 (default): the
+                                  autotuner's choice per degree class; 4, 8, 16, 32:
+                                  that many lanes per row, rows held in registers
+                                  (a market whose longest row does not fit takes the
+                                  narrowest width that fits, or the chunked path);
+                                  64: the chunked long-row path (32 lanes streaming
+                                  the row) for every market.  Other values:
+                                  PDHCG_ERR_INVALID                                  */
 } pdhcg_params;
 
 typedef struct {

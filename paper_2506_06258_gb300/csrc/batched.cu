@@ -639,6 +639,10 @@ pdhcg_status pdhcg_fisher_solve_batched(pdhcg_handle h, int32_t B, const int64_t
         return PDHCG_ERR_INVALID;
     if (!(prm->tol > 0) || prm->max_iter <= 0 || prm->kkt_check_every <= 0 || prm->row_solve_max_iter <= 0)
         return PDHCG_ERR_INVALID;
+    {
+        const int bl = prm->batch_lanes;
+        if (bl != 0 && bl != 4 && bl != 8 && bl != 16 && bl != 32 && bl != 64) return PDHCG_ERR_INVALID;
+    }
     enter(h);
     h->state.valid = false;
     cudaStream_t s = h->stream;
@@ -776,6 +780,17 @@ pdhcg_status pdhcg_fisher_solve_batched(pdhcg_handle h, int32_t B, const int64_t
         members[cls[b]].push_back(b);
     }
     int* table = mixed ? h->bt_table_mixed : h->bt_table_fp64;
+    int forced[5] = {-1, -1, -1, -1, -1};
+    if (prm->batch_lanes) {
+        // a caller's width for every class whose rows fit it (classes are
+        // ordered by the width their longest rows need; 0 = chunked)
+        const int cand[5] = {4, 8, 16, 32, 0};
+        for (int c = 0; c < 5; c++) {
+            if (prm->batch_lanes == 64 || c == 4) forced[c] = 0;
+            else forced[c] = std::max(prm->batch_lanes, cand[c]);
+        }
+        table = forced;
+    }
     const int cand_g[5] = {4, 8, 16, 32, 0};
     bool tuned = false;
     for (int c = 0; c < 5; c++) {
