@@ -40,3 +40,36 @@ def test_oracle_reproduces_stored_prices():
     assert r.converged
     assert np.max(np.abs(r.p - g["p"]) / g["p"]) <= 1e-8
     assert np.max(np.abs(r.t - g["t"]) / g["t"]) <= 1e-8
+
+
+def _c3law():
+    import sys, os
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    from make_golden import c3law_market
+    return c3law_market(), load_equilibrium("c3law_equilibrium.txt")
+
+
+def test_stored_c3law_prices_satisfy_the_dual_equilibrium_conditions():
+    """The stored benchmark-law equilibrium (p, t; no allocation is stored) meets
+    the conditions that involve p and t alone: money is conserved (sum p =
+    sum w, Fact 1), no buyer sees a bang-per-buck above y_i = w_i / t_i
+    (p_j >= u_ij y_i, the KKT system of Section 2), and every buyer's best
+    bang-per-buck is reached (each buyer spends on some good with p_j = u_ij y_i)."""
+    mk, g = _c3law()
+    p, t = g["p"], g["t"]
+    assert len(p) == mk.m and len(t) == mk.n
+    val = mk.val.astype(np.float64)
+    rows = F.row_ids(mk.row_ptr)
+    y = mk.w / t
+    ratio = val * y[rows] / p[mk.col]                 # u_ij y_i / p_j <= 1, = 1 on the support
+    best = np.full(mk.n, -np.inf)
+    np.maximum.at(best, rows, ratio)
+    assert abs(p.sum() - mk.w.sum()) / mk.w.sum() <= 1e-9
+    assert np.max(ratio) <= 1 + 1e-7
+    assert np.max(np.abs(best - 1.0)) <= 1e-7
+    # a planted 1e-4 error in one price breaks the conditions
+    j = int(np.argmax(p))
+    p2 = p.copy()
+    p2[j] *= 1 - 1e-4
+    ratio2 = val * y[rows] / p2[mk.col]
+    assert np.max(ratio2) > 1 + 1e-5
