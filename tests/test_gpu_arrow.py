@@ -18,10 +18,14 @@ def solver():
     s.close()
 
 
-@pytest.mark.parametrize("prec,tol,outer,rtol", [("fp64", 1e-9, 1e-7, 1e-5), ("mixed", 1e-6, 1e-5, 1e-4)])
+@pytest.mark.parametrize("prec,tol,outer,rtol", [("fp64", 1e-9, 1e-7, 1e-5), ("mixed", 1e-7, 1e-6, 1e-5),
+                                                  ("mixed", 1e-6, 1e-5, 1e-4)])
 def test_exchange_identity_endowments(solver, prec, tol, outer, rtol):
-    """MIXED inner solves stop at relative KKT 1e-6, so the outer change cannot
-    be driven far below that; its tolerances follow."""
+    """The fixed point of Alg. 4 to a relative budget change of 1e-6 with
+    prices within 1e-5 of the oracle's, in both precisions: the MIXED inner
+    solves run to relative KKT 1e-7 (FP32 iterates reach about 5e-8), below the
+    outer tolerance.  With inner solves stopped at 1e-6 the outer change cannot
+    be driven far below that, and the last case's tolerances follow."""
     mk = S.config4(n=60, d_other=6, seed=500)
     ref = arrow.ad_fixed_point(mk.row_ptr, mk.col, mk.val, mk.w, mk.m, outer_tol=1e-9, inner_tol=1e-11)
     out = solver.ad_solve(dev(mk.row_ptr), dev(mk.col), dev(mk.val), dev(mk.w), mk.m, outer_tol=outer,
