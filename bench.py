@@ -612,6 +612,46 @@ def _time_to_tol_c2(solver, capi, torch, stream, dev, S, limit_s):
     return res
 
 
+# the paper's Table tab:random-fisher rows (n, m, density; PDHCG and PDHG iterations and seconds on its GPU, to 1e-4)
+_RANDOM_FISHER_PAPER = (((1000, 400, 0.2), (2612, 1.7, 4303.8, 4.5)), ((10000, 4000, 0.02), (2758, 3.6, 7604, 7.1)),
+                        ((100000, 4000, 0.02), (1200, 8.3, 10463, 29.9)))
+
+
+def _study_pdhg(sol, S):
+    """Restarted PDHG (Alg. 1, FP64, restart every 1000 steps) against PDHCG
+    (Alg. 2, FP64 and MIXED) on the same GPU, on the Section 5.1 instances of
+    Table tab:random-fisher up to n = 1e5: iterations and seconds to the
+    paper's relative KKT 1e-4 and to 1e-6 (180 s cap each).  The paper's own
+    iterations and times (other hardware) ride along as context."""
+    import torch
+    out = {"workload": "Table tab:random-fisher instances (Section 5.1 law: w~U(0,1), u_ij nonzero w.p. density, "
+                       "then U(0,1))", "sizes": []}
+    for k, ((n, m, q), paper) in enumerate(_RANDOM_FISHER_PAPER):
+        mk = S.paper_synthetic(n, m, q, seed=S.SEED_BASE + 60 + k)
+        rp, col, w = _dev(mk.row_ptr), _dev(mk.col), _dev(mk.w)
+        v64, v32 = _dev(mk.val.astype(np.float64)), _dev(mk.val.astype(np.float32))
+        row = {"n": n, "m": m, "density": q, "nnz": int(mk.nnz), "paper_pdhcg_iters": paper[0],
+               "paper_pdhcg_s": paper[1], "paper_pdhg_iters": paper[2], "paper_pdhg_s": paper[3]}
+        for tol in (1e-4, 1e-6):
+            for name, fn in (("pdhg_fp64", lambda t: sol.fisher_solve_pdhg(rp, col, v64, w, m, tol=t, check=False,
+                                                                            max_iter=10_000_000, time_limit_s=180.0)),
+                             ("pdhcg_fp64", lambda t: sol.fisher_solve(rp, col, v64, w, m, tol=t, precision="fp64",
+                                                                       check=False, max_iter=10_000_000,
+                                                                       time_limit_s=180.0)),
+                             ("pdhcg_mixed", lambda t: sol.fisher_solve(rp, col, v32, w, m, tol=t, precision="mixed",
+                                                                        check=False, max_iter=10_000_000,
+                                                                        time_limit_s=180.0))):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                o = fn(tol)
+                torch.cuda.synchronize()
+                row[f"{name}_tol_{tol:.0e}"] = {"status": int(o.status), "seconds": time.perf_counter() - t0,
+                                                "iters": int(o.info["iters"]), "kkt": o.info["kkt"]}
+        out["sizes"].append(row)
+        print(json.dumps({"study": "pdhg", "partial": True, **row}), flush=True)
+    return out
+
+
 def run_study(which):
     import torch
     import __graft_entry__ as g
@@ -620,7 +660,7 @@ def run_study(which):
     torch.cuda.set_device(0)
     sol = api.Solver()
     fn = {"c2": _study_c2, "c4": _study_c4, "c5": _study_c5, "jd": _study_jd, "ad": _study_ad,
-          "sections": _study_sections}[which]
+          "sections": _study_sections, "pdhg": _study_pdhg}[which]
     out = fn(sol, S)
     sol.close()
     print(json.dumps({"study": which, **out}), flush=True)
@@ -642,7 +682,7 @@ def main():
     ap.add_argument("--ttt-limit-s", type=float, default=300.0, help="time cap of the time-to-tolerance solve")
     ap.add_argument("--no-fp64-arm", dest="fp64_arm", action="store_false",
                     help="skip the plain FP64 GPU iterations/s on the same workload (on by default)")
-    ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad", "sections"], default=None,
+    ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad", "sections", "pdhg"], default=None,
                     help="instead of the bench line, run one comparison study and print its JSON line")
     args = ap.parse_args()
 

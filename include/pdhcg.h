@@ -234,6 +234,24 @@ pdhcg_status pdhcg_fisher_backward(pdhcg_handle h, const double* grad_p, const d
                                    double* grad_u, double* grad_w);
 
 /* ---------------------------------------------------------------------------
+ * Restarted PDHG (Alg. 1, Section 2.1), the paper's comparator for PDHCG, in
+ * FP64 whatever prm->prec says.  The saddle form keeps the buyer utilities t
+ * as primal variables with dual variables y for t_i = u_i^T x_i; each step is
+ * the closed-form update of Eq. update:py (p and y), Eq. update:t (t) and Eq.
+ * update:x (x = [x - tau (p - u y)]_+).  Every restart_every steps the iterates
+ * restart from their uniform averages (Alg. 1).  Constant step sizes tau =
+ * eta / omega, sigma = eta omega with eta = prm->eta0_scale / ||K||_2 (||K||_2
+ * by power iteration on the GPU) and omega = ||p^0|| / ||(x^0, t^0)||.  Stops
+ * when the relative KKT error of Section 5 of the current point or of the
+ * average is <= prm->tol (checked every prm->kkt_check_every steps), or on
+ * prm->max_iter / prm->time_limit_s.  Outputs as pdhcg_fisher_solve (x_out is
+ * double); the equilibrium it returns is saved for pdhcg_fisher_backward.
+ * ------------------------------------------------------------------------- */
+pdhcg_status pdhcg_fisher_solve_pdhg(pdhcg_handle h, const pdhcg_market* mk, const pdhcg_params* prm,
+                                     int32_t restart_every, double* p_out, double* util_out, void* x_out,
+                                     pdhcg_info* info);
+
+/* ---------------------------------------------------------------------------
  * Building blocks of one iteration, exposed so that each step can be checked
  * on its own at any size.  They run the same kernels as the solver.
  *

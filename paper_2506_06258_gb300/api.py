@@ -118,6 +118,21 @@ class Solver:
             raise capi.PdhcgError(st, "pdhcg_fisher_solve")
         return SolveOutput(p, util, x, info.as_dict(), st)
 
+    def fisher_solve_pdhg(self, row_ptr, col, val, w, m, tol=1e-6, restart_every=1000, return_x=False, check=True,
+                          **prm) -> SolveOutput:
+        """Restarted PDHG (Alg. 1) in FP64 on the GPU: pdhcg_fisher_solve_pdhg."""
+        mk = self.market(row_ptr, col, val, w, m)
+        params = capi.default_params(tol=tol, prec=capi.PDHCG_FP64, **prm)
+        ref = mk._keep[0]
+        p = _empty_like_loc(ref, m, np.float64)
+        util = _empty_like_loc(ref, mk.n, np.float64)
+        x = _empty_like_loc(ref, mk.nnz, np.float64) if return_x else None
+        info = capi.pdhcg_info()
+        st = capi.pdhcg_fisher_solve_pdhg(self.h, mk, params, restart_every, _ptr(p), _ptr(util), _ptr(x), info)
+        if check and st not in (capi.PDHCG_OK, capi.PDHCG_ERR_NOT_CONVERGED):
+            raise capi.PdhcgError(st, "pdhcg_fisher_solve_pdhg")
+        return SolveOutput(p, util, x, info.as_dict(), st)
+
     def ad_solve(self, row_ptr, col, val, w0, m, E=None, outer_tol=1e-6, max_outer=100, tol=1e-8,
                  precision="mixed", check=True, **prm):
         mk = self.market(row_ptr, col, val, w0, m)

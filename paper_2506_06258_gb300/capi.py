@@ -55,6 +55,8 @@ _SIGS = {
     "pdhcg_destroy": (ctypes.c_int, [c_void_p]),
     "pdhcg_fisher_solve": (ctypes.c_int, [c_void_p, _P(pdhcg_market), _P(pdhcg_params), c_void_p, c_void_p,
                                           c_void_p, c_void_p, c_void_p, _P(pdhcg_info)]),
+    "pdhcg_fisher_solve_pdhg": (ctypes.c_int, [c_void_p, _P(pdhcg_market), _P(pdhcg_params), c_int32, c_void_p,
+                                               c_void_p, c_void_p, _P(pdhcg_info)]),
     "pdhcg_fisher_begin": (ctypes.c_int, [c_void_p, _P(pdhcg_market), _P(pdhcg_params), c_void_p, c_void_p]),
     "pdhcg_fisher_step": (ctypes.c_int, [c_void_p, c_int32, _P(pdhcg_info)]),
     "pdhcg_fisher_end": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, _P(pdhcg_info)]),
@@ -145,6 +147,12 @@ def pdhcg_fisher_solve(h, mk, prm, p0, x0, p_out, util_out, x_out, info) -> int:
     return _fn("pdhcg_fisher_solve")(c_void_p(h), ctypes.byref(mk), ctypes.byref(prm), c_void_p(p0), c_void_p(x0),
                                      c_void_p(p_out), c_void_p(util_out), c_void_p(x_out),
                                      ctypes.byref(info) if info is not None else None)
+
+
+def pdhcg_fisher_solve_pdhg(h, mk, prm, restart_every, p_out, util_out, x_out, info) -> int:
+    return _fn("pdhcg_fisher_solve_pdhg")(c_void_p(h), ctypes.byref(mk), ctypes.byref(prm), c_int32(restart_every),
+                                          c_void_p(p_out), c_void_p(util_out), c_void_p(x_out),
+                                          ctypes.byref(info) if info is not None else None)
 
 
 def pdhcg_fisher_begin(h, mk, prm, p0, x0) -> int:

@@ -287,7 +287,7 @@ pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, 
 // ---------------------------------------------------------------------------
 // iteration workspace
 // ---------------------------------------------------------------------------
-static pdhcg_status alloc_iter(pdhcg_handle h) {
+pdhcg_status alloc_iter(pdhcg_handle h) {
     Prepared& P = h->prep;
     const size_t vb = P.mixed ? 4 : 8;
     const int m = P.m, n = P.n;
@@ -340,7 +340,7 @@ static IterBufs iter_bufs(pdhcg_handle h) {
     return b;
 }
 
-static KktBufs kkt_bufs(pdhcg_handle h, double* c_out, double* t_out, int slot) {
+KktBufs kkt_bufs(pdhcg_handle h, double* c_out, double* t_out, int slot) {
     KktBufs k = {};
     k.acc = (unsigned long long*)h->acc.p;
     k.M = (unsigned long long*)h->M.p;

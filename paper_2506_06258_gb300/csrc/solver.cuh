@@ -130,6 +130,7 @@ struct pdhcg_handle_s {
     double tight_kappa = 0.0;   // 0: automatic (from the KKT error of the solve)
     double bt_kkt_max = 0.0;    // largest KKT error of the last batched solve
     pdhcg::DevBuf adj[24];
+    pdhcg::DevBuf pd[16];         // restarted PDHG (pdhg.cu)
     pdhcg::HostMirror* host = nullptr;
 
     void release() {
@@ -141,12 +142,17 @@ struct pdhcg_handle_s {
         for (auto* b : all) b->release();
         for (auto& b : bt) b.release();
         for (auto& b : adj) b.release();
+        for (auto& b : pd) b.release();
         if (host) cudaFreeHost(host);
         host = nullptr;
     }
 };
 
 pdhcg_status prepare_market(pdhcg_handle h, const pdhcg_market* mk, bool mixed, bool init_x);
+// iteration workspace of a prepared market (shared with the PDHG solver)
+pdhcg_status alloc_iter(pdhcg_handle h);
+// buffers of one KKT evaluation (slot 0: current point, 1: average)
+pdhcg::KktBufs kkt_bufs(pdhcg_handle h, double* c_out, double* t_out, int slot);
 // Order the library stream after the caller's legacy default stream (a graph
 // cannot be captured on stream 0, so such handles work on a stream of their own).
 void enter(pdhcg_handle h);
