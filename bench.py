@@ -519,24 +519,29 @@ _SECTIONS_PAPER = (((100000, 4000, 0.5), (247.3, 163.2, 131.0, 113.3, 95.9, 172.
 
 
 def _study_sections(sol, S):
-    """Average iteration time of the exact row root (FP64 and MIXED) on the
-    instances of Table diff_division (Section 5.1 law: w~U(0,1), u_ij nonzero
-    with the given density, then U(0,1)): 3 check periods of 64 accepted
-    iterations after one warm-up period, CUDA events around them.  The paper's
-    K-section times (other hardware) ride along as context."""
+    """Average iteration time on the instances of Table diff_division (Section
+    5.1 law: w~U(0,1), u_ij nonzero with the given density, then U(0,1)) with
+    the paper's K-section row search (FP64, K = 2, 4, 8, 16, 32, 64, bracket
+    tolerance 1e-8 as in the paper) beside the exact row root (FP64 and MIXED):
+    one warm-up check period of 16 iterations, then one timed (host clock
+    around the synchronous step; the row kernel's own time by CUDA events
+    inside the graph).  The paper's K-section times (other hardware) ride along."""
     import torch
     from paper_2506_06258_gb300 import capi
-    out = {"workload": "Table diff_division instances (Section 5.1 law), exact row root", "sizes": []}
+    out = {"workload": "Table diff_division instances (Section 5.1 law)", "sizes": []}
     for k, ((n, m, q), paper_ms) in enumerate(_SECTIONS_PAPER):
         mk = S.paper_synthetic(n, m, q, seed=S.SEED_BASE + 40 + k)
         row = {"n": n, "m": m, "density": q, "nnz": int(mk.nnz),
                "paper_ms_per_iter_by_sections": dict(zip(("2", "4", "8", "16", "32", "64"), paper_ms))}
         rp, col, w = _dev(mk.row_ptr), _dev(mk.col), _dev(mk.w)
-        for prec in ("fp64", "mixed"):
-            val = _dev(mk.val.astype(np.float64 if prec == "fp64" else np.float32))
+        v64 = _dev(mk.val.astype(np.float64))
+        v32 = _dev(mk.val.astype(np.float32))
+        runs = [("exact_mixed", v32, capi.PDHCG_MIXED, 0)] + [("exact_fp64", v64, capi.PDHCG_FP64, 0)] + \
+               [(f"sections_{K}_fp64", v64, capi.PDHCG_FP64, K) for K in (2, 4, 8, 16, 32, 64)]
+        for name, val, prec, K in runs:
             market = sol.market(rp, col, val, w, m)
-            prm = capi.default_params(tol=1e-12, prec=capi.PDHCG_FP64 if prec == "fp64" else capi.PDHCG_MIXED,
-                                      timing=1)
+            prm = capi.default_params(tol=1e-12, prec=prec, timing=1, kkt_check_every=16, section_count=K,
+                                      section_tol=1e-8)
             st = capi.pdhcg_fisher_begin(sol.h, market, prm, None, None)
             if st:
                 raise capi.PdhcgError(st, "pdhcg_fisher_begin")
@@ -544,72 +549,17 @@ def _study_sections(sol, S):
             capi.pdhcg_fisher_step(sol.h, 1, i0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            capi.pdhcg_fisher_step(sol.h, 3, i1)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
+            capi.pdhcg_fisher_step(sol.h, 1, i1)          # synchronous: returns after its check period
+            dt = (time.perf_counter() - t0) * 1e3
             its = i1.iters - i0.iters
-            row[prec] = {"ms_per_iter": 1e3 * dt / max(its, 1), "iters": int(its),
-                         "row_pass_ms": (i1.prox_ms - i0.prox_ms) / max(i1.prox_launches - i0.prox_launches, 1)}
+            row[name] = {"ms_per_iter": dt / max(its, 1), "iters": int(its),
+                         "row_pass_ms": (i1.prox_ms - i0.prox_ms) / max(i1.prox_launches - i0.prox_launches, 1),
+                         "capped_rows": int(i1.row_solve_capped)}
             capi.pdhcg_fisher_end(sol.h, None, None, None, None)
-            del val
         out["sizes"].append(row)
         print(json.dumps({"study": "sections", "partial": True, **row}), flush=True)
+        del v64, v32
     return out
-
-
-def _gpu_iter_rate(solver, capi, torch, stream, rp, col, val, w, m, prec, nnz, warm=1, timed=1):
-    """Iterations/s of one precision on a device-resident market: `warm`
-    check periods untimed, then `timed` check periods between CUDA events."""
-    market = solver.market(rp, col, val, w, m)
-    prm = capi.default_params(tol=1e-6, prec=prec, timing=1)
-    st = capi.pdhcg_fisher_begin(solver.h, market, prm, None, None)
-    if st:
-        raise capi.PdhcgError(st, "pdhcg_fisher_begin")
-    i0, i1 = capi.pdhcg_info(), capi.pdhcg_info()
-    capi.pdhcg_fisher_step(solver.h, warm, i0)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    capi.pdhcg_fisher_step(solver.h, timed, i1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    its = i1.iters - i0.iters
-    launches = max(i1.prox_launches - i0.prox_launches, 1)
-    row_ms = (i1.prox_ms - i0.prox_ms) / launches
-    capi.pdhcg_fisher_end(solver.h, None, None, None, None)
-    bpe = 44.0 if prec == capi.PDHCG_FP64 else 24.0
-    return {"iters_per_s": its / (ms * 1e-3) if ms > 0 else 0.0, "iters_timed": int(its), "ms": ms,
-            "row_kernel_ms": row_ms, "alg_bytes_per_iter": bpe * nnz,
-            "achieved_GB_per_s": bpe * nnz / (ms * 1e-3 / max(its, 1)) / 1e9}
-
-
-def _time_to_tol_c2(solver, capi, torch, stream, dev, S, limit_s):
-    """C2 (n = 1e6 buyers, m = 1e4 goods, 100 distinct uniform goods per buyer,
-    nnz = 1e8, LogNormal(0,1) utilities, w ~ U(0.5,1.5)): one MIXED solve to
-    relative KKT 1e-6 from device-resident inputs (validation, preprocessing and
-    the iteration loop timed), with the GPU's own Section 5 residuals of the
-    returned point; and FP64 iterations/s on the same market."""
-    mk = S.config2(fp32=True)
-    rp, col, w = (torch.from_numpy(a).to(dev) for a in (mk.row_ptr, mk.col, mk.w))
-    val = torch.from_numpy(mk.val).to(dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = solver.fisher_solve(rp, col, val, w, mk.m, tol=1e-6, precision="mixed", check=False,
-                              time_limit_s=limit_s)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    i = out.info
-    res = {"workload": "C2: n=1e6, m=1e4, 100 distinct uniform goods per buyer (nnz=1e8), LogNormal(0,1), "
-                       "w~U(0.5,1.5), MIXED, relative KKT 1e-6", "nnz": int(mk.nnz), "seconds": dt,
-           "status": int(out.status), "converged": int(out.status) == 0, "iters": int(i["iters"]),
-           "restarts": int(i["restarts"]), "kkt": i["kkt"], "r_primal": i["r_primal"], "r_dual": i["r_dual"],
-           "r_gap": i["r_gap"], "setup_s": i["setup_ms"] * 1e-3, "loop_s": i["solve_ms"] * 1e-3}
-    val64 = torch.from_numpy(mk.val.astype(np.float64)).to(dev)
-    res["fp64_iters_per_s"] = _gpu_iter_rate(solver, capi, torch, stream, rp, col, val64, w, mk.m,
-                                             capi.PDHCG_FP64, mk.nnz)["iters_per_s"]
-    res["mixed_iters_per_s"] = i["iters"] / max(i["solve_ms"] * 1e-3, 1e-9)
-    return res
 
 
 # the paper's Table tab:random-fisher rows (n, m, density; PDHCG and PDHG iterations and seconds on its GPU, to 1e-4)

@@ -108,6 +108,13 @@ typedef struct {
                                   64: the chunked long-row path (32 lanes streaming
                                   the row) for every market.  Other values:
                                   PDHCG_ERR_INVALID                                  */
+    int32_t section_count;     /* FP64 single-market solves: 0 (default) = the exact
+                                  active-set root of each row subproblem; K >= 2 = the
+                                  K-section search of Section 2.2 (K candidates per
+                                  round, each with its image bracketing the root),
+                                  at most row_solve_max_iter rounds                  */
+    double section_tol;        /* relative bracket width at which the K-section
+                                  search stops (0 = 1e-8, the paper's)               */
 } pdhcg_params;
 
 typedef struct {

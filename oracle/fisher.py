@@ -227,8 +227,9 @@ def bisection_search(u, a, cc, s0, eps=1e-12, max_rounds=200):
 
 def section_search(u, a, cc, s0, sections=32, eps=1e-12, max_rounds=200):
     """The K-section search of Section 2.2 (K = 32 in the paper): candidates
-    s_l = (1 - l/(K+1)) L + l/(K+1) U, l = 1..K; U <- min(U, max_l max(s_l, s~_l)),
-    L <- max(L, min_l min(s_l, s~_l))."""
+    s_l = (1 - l/(K+1)) L + l/(K+1) U, l = 1..K; each candidate and its image
+    s~_l bracket the root, so U <- min(U, min_l max(s_l, s~_l)) and
+    L <- max(L, max_l min(s_l, s~_l))."""
     def img(s):
         return float(np.dot(u, np.maximum(a + cc / s, 0.0)))
     s = s0

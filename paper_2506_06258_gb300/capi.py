@@ -31,7 +31,8 @@ class pdhcg_params(ctypes.Structure):
                 ("beta_art", c_double), ("theta", c_double), ("eta_lo", c_double), ("eta_hi", c_double),
                 ("eta0_scale", c_double), ("omega_reset_every", c_int32), ("omega_range", c_double),
                 ("row_solve_max_iter", c_int32), ("tight_kappa", c_double), ("verbose", c_int32),
-                ("timing", c_int32), ("batch_lanes", c_int32)]
+                ("timing", c_int32), ("batch_lanes", c_int32),
+                ("section_count", c_int32), ("section_tol", c_double)]
 
 
 class pdhcg_info(ctypes.Structure):

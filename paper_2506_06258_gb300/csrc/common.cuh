@@ -64,6 +64,8 @@ struct Ctl {
     double xf_w1, xf_w2;
     int xf_n;
     int xf_folded;         // the waiting pair has been folded (set by the fold kernel's last block)
+    int sections;          // FP64 row solve: 0 exact root, K >= 2 K-section search (Section 2.2)
+    double sec_tol;        // relative bracket width that ends the K-section search
     unsigned int xf_ticket;   // last-block-done counter of the fold kernel
     int pad2;
     unsigned long long work[kMaxBuckets];   // dynamic work counters of the row kernel

@@ -77,6 +77,8 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     rc.fold_w = (float)rc.fold_wd;
     rc.cap = ctl->row_cap;
     rc.seed = mix32((unsigned)ctl->passes * 2u + 1u);
+    rc.sections = ctl->sections;
+    rc.sec_tol = ctl->sec_tol;
     RowCtxM rm;       // MIXED: x-bar is folded by fold_pair_kernel, not here
     rm.tau = rc.tau_hi;
     rm.cap = rc.cap;
@@ -512,6 +514,7 @@ __global__ void ctl_fixed_kernel(Ctl* ctl, double tau, int cap) {
     ctl->tau = tau;
     ctl->fold_pending = 0;
     ctl->xf_n = 0;
+    ctl->sections = 0;
     ctl->cur = 0;
     ctl->row_cap = cap;
     ctl->capped = 0;

@@ -49,6 +49,8 @@ struct RowCtx {
     bool fold;
     int cap;
     unsigned seed;      // pass counter mixed into the stochastic-rounding bits
+    int sections = 0;   // FP64: 0 = exact active-set root, K >= 2 = K-section search
+    double sec_tol = 1e-8;
 };
 
 // ---------------------------------------------------------------------------
@@ -597,6 +599,45 @@ __device__ void row_fp64(const DevMarket& mk, const double* __restrict__ U, cons
     double s = s0, s_last = -1.0;
     bool gdone = !valid;
     int rounds = 0;
+    if (rc.sections > 0) {
+        // K-section search of Section 2.2: s* lies between any s and its image
+        // s~(s) = sum_j u_j [a_j + tw u_j / s]_+ (s~ is decreasing), so each of
+        // the K candidates s_l = L + l (U - L) / (K + 1) with its image brackets
+        // the root: U <- min_l max(s_l, s~_l), L <- max_l min(s_l, s~_l); stop
+        // when U - L <= sec_tol U; s = (L + U) / 2
+        auto img = [&](double sv) -> double {
+            const double R = tw / sv;
+            double acc = 0.0;
+            for (int c = 0; c < nch; c++) {
+                if (LONG) load_chunk(c);
+#pragma unroll
+                for (int k = 0; k < kSlots; k++)
+                    if (rin[k]) acc = fma(ru[k], fmax(fma(ru[k], R, ra[k]), 0.0), acc);
+            }
+            return group_sum<G>(acc);
+        };
+        const double st0 = img(s0);
+        double U = fmax(s0, st0), L = fmin(s0, st0);
+        if (!(U - L > rc.sec_tol * U)) gdone = true;
+        const int K = rc.sections;
+        while (__any_sync(0xffffffffu, !gdone)) {
+            double nU = U, nL = L;
+            for (int l = 1; l <= K; l++) {
+                const double sl = fmax(L + (U - L) * ((double)l / (double)(K + 1)), 1e-300);
+                const double st = img(sl);
+                nU = fmin(nU, fmax(sl, st));
+                nL = fmax(nL, fmin(sl, st));
+            }
+            if (!gdone) {
+                U = nU;
+                L = nL;
+                if (!(U - L > rc.sec_tol * U)) gdone = true;
+                else if (++rounds >= rc.cap) { gdone = true; if (tl == 0 && valid) capped++; }
+            }
+        }
+        s = 0.5 * (U + L);
+        gdone = true;
+    }
     while (__any_sync(0xffffffffu, !gdone)) {
         const double R = tw / s;
         double A = 0.0, Q = 0.0;

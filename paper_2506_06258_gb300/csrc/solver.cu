@@ -435,6 +435,8 @@ pdhcg_status session_begin(pdhcg_handle h, const pdhcg_params& prm, const double
     c0.active = 1;
     c0.chunk_quota = prm.kkt_check_every;
     c0.row_cap = prm.row_solve_max_iter;
+    c0.sections = mixed ? 0 : prm.section_count;     // the K-section search is an FP64 row solve
+    c0.sec_tol = prm.section_tol > 0 ? prm.section_tol : 1e-8;
     CK(cudaMemcpyAsync(h->ctl.p, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     IterBufs bf = iter_bufs(h);
     Ctl* ctl = (Ctl*)h->ctl.p;
@@ -745,6 +747,8 @@ static pdhcg_status check_params(const pdhcg_params* prm) {
         return PDHCG_ERR_INVALID;
     if (!(prm->eta_lo > 0) || !(prm->eta_hi >= prm->eta_lo) || !(prm->eta0_scale > 0)) return PDHCG_ERR_INVALID;
     if (prm->prec != PDHCG_FP64 && prm->prec != PDHCG_MIXED) return PDHCG_ERR_INVALID;
+    if (prm->section_count < 0 || prm->section_count == 1 || prm->section_count > 1024 || prm->section_tol < 0)
+        return PDHCG_ERR_INVALID;
     return PDHCG_OK;
 }
 
