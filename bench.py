@@ -122,7 +122,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("prox.cu", "rowsolve.cuh", "common.cuh"):
+    for f in ("prox.cu", "rowsolve.cuh", "rowsolve_mixed.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2506_06258_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
