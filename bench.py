@@ -364,7 +364,7 @@ def _study_c5(sol, S):
     """256 markets of the C5 law (n~UI[50,5000], m~UI[20,2000],
     density~U(0.05,0.3)): one batched persistent launch to tolerance 1e-6 (120 s cap),
     MIXED and FP64; the batched backward of sum p.r; a loop of single-market
-    solves on 16 markets."""
+    solves on 16 markets (30 s cap each)."""
     import torch
     from paper_2506_06258_gb300 import capi
     bt = S.config5(B=256)
@@ -404,7 +404,7 @@ def _study_c5(sol, S):
     for b in range(16):
         mk = bt.market(b)
         sol.fisher_solve(_dev(mk.row_ptr), _dev(mk.col), _dev(mk.val.astype(np.float32)), _dev(mk.w), mk.m,
-                         tol=1e-6, precision="mixed", check=False)
+                         tol=1e-6, precision="mixed", check=False, time_limit_s=30.0)
     torch.cuda.synchronize()
     loop = time.perf_counter() - t0
     out["single_solve_loop_16_markets_seconds"] = loop
@@ -486,7 +486,7 @@ def _study_ad(sol, S):
     """Arrow-Debreu with random sparse endowments (Section 5.3, inside Thm 2's
     assumptions): the instances of Table tab:arrow-debreu up to n = 1e6, MIXED
     fixed point to a relative budget change < 1e-4 with inner solves to 1e-6,
-    300 s cap each.  The n = 1e7 row (about 1.2e9 nonzeros in U and E) is left
+    120 s cap each.  The n = 1e7 row (about 1.2e9 nonzeros in U and E) is left
     out.  The paper's iterations and times (other hardware) ride along."""
     import torch
     out = {"workload": "Arrow-Debreu, U and E Bernoulli-sparse with U(0,1) entries, E columns summing to 1, "
@@ -499,7 +499,7 @@ def _study_ad(sol, S):
         t0 = time.perf_counter()
         o = sol.ad_solve(_dev(mk.row_ptr), _dev(mk.col), _dev(mk.val), _dev(mk.w), m,
                          E=(_dev(erp), _dev(ecol.astype(np.int32)), _dev(ev)), outer_tol=1e-4, tol=1e-6,
-                         precision="mixed", max_outer=200, check=False, time_limit_s=300.0)
+                         precision="mixed", max_outer=200, check=False, time_limit_s=120.0)
         torch.cuda.synchronize()
         row.update({"status": int(o.status), "seconds": time.perf_counter() - t0, "outer": int(o.info["outer"]),
                     "inner_iters": int(o.info["iters"]), "kkt": o.info["kkt"]})
