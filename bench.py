@@ -562,6 +562,95 @@ def _study_sections(sol, S):
     return out
 
 
+def _gpu_iter_rate(solver, capi, torch, stream, rp, col, val, w, m, prec, nnz, warm=1, timed=1):
+    """Iterations/s of one precision on a device-resident market: `warm`
+    check periods untimed, then `timed` check periods between CUDA events."""
+    market = solver.market(rp, col, val, w, m)
+    prm = capi.default_params(tol=1e-6, prec=prec, timing=1)
+    st = capi.pdhcg_fisher_begin(solver.h, market, prm, None, None)
+    if st:
+        raise capi.PdhcgError(st, "pdhcg_fisher_begin")
+    i0, i1 = capi.pdhcg_info(), capi.pdhcg_info()
+    capi.pdhcg_fisher_step(solver.h, warm, i0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    capi.pdhcg_fisher_step(solver.h, timed, i1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = i1.iters - i0.iters
+    launches = max(i1.prox_launches - i0.prox_launches, 1)
+    row_ms = (i1.prox_ms - i0.prox_ms) / launches
+    capi.pdhcg_fisher_end(solver.h, None, None, None, None)
+    bpe = 44.0 if prec == capi.PDHCG_FP64 else 24.0
+    return {"iters_per_s": its / (ms * 1e-3) if ms > 0 else 0.0, "iters_timed": int(its), "ms": ms,
+            "row_kernel_ms": row_ms, "alg_bytes_per_iter": bpe * nnz,
+            "achieved_GB_per_s": bpe * nnz / (ms * 1e-3 / max(its, 1)) / 1e9}
+
+
+def _stored_equilibrium(name):
+    """p and t of a stored oracle equilibrium (tests/golden, written by the
+    committed tests/golden/make_golden.py from the FP64 oracle)."""
+    out, lines = {}, open(os.path.join(ROOT, "tests", "golden", name)).read().splitlines()
+    i = 0
+    while i < len(lines):
+        if lines[i].startswith("#"):
+            i += 1
+            continue
+        key, cnt = lines[i].split()
+        out[key] = np.array([float(v) for v in lines[i + 1:i + 1 + int(cnt)]])
+        i += 1 + int(cnt)
+    return out
+
+
+def _oracle_parity_c3law(solver, torch, dev, S):
+    """The benchmark law at 1/1000 scale (n = 1e4, m = 1e3, nnz ~ 9.2e5, the
+    stored oracle equilibrium's market): MIXED GPU solves to relative KKT 1e-6
+    and 2e-7, maximum relative price and utility error against the stored
+    equilibrium of the FP64 oracle (relative KKT 8.7e-10)."""
+    g = _stored_equilibrium("c3law_equilibrium.txt")
+    mk = S.config3(n=10_000, m=1_000, nnz_target=1_000_000, fp32=True)
+    args = [torch.from_numpy(a).to(dev) for a in (mk.row_ptr, mk.col, mk.val, mk.w)]
+    res = {"workload": "benchmark law at n=1e4, m=1e3 (nnz=%d), MIXED, against the stored FP64 oracle "
+                       "equilibrium (tests/golden/c3law_equilibrium.txt)" % mk.nnz}
+    for tol in (1e-6, 2e-7):
+        o = solver.fisher_solve(*args, mk.m, tol=tol, precision="mixed", check=False)
+        p, t = o.p.cpu().numpy(), o.util.cpu().numpy()
+        res[f"tol_{tol:.0e}"] = {"status": int(o.status), "iters": int(o.info["iters"]), "kkt": o.info["kkt"],
+                                 "price_rel_err_max": float(np.max(np.abs(p - g["p"]) / g["p"])),
+                                 "util_rel_err_max": float(np.max(np.abs(t - g["t"]) / g["t"]))}
+    return res
+
+
+def _time_to_tol_c2(solver, capi, torch, stream, dev, S, limit_s):
+    """C2 (n = 1e6 buyers, m = 1e4 goods, 100 distinct uniform goods per buyer,
+    nnz = 1e8, LogNormal(0,1) utilities, w ~ U(0.5,1.5)): one MIXED solve to
+    relative KKT 1e-6 from device-resident inputs (validation, preprocessing and
+    the iteration loop timed), with the GPU's own Section 5 residuals of the
+    returned point; and FP64 iterations/s on the same market."""
+    mk = S.config2(fp32=True)
+    rp, col, w = (torch.from_numpy(a).to(dev) for a in (mk.row_ptr, mk.col, mk.w))
+    val = torch.from_numpy(mk.val).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = solver.fisher_solve(rp, col, val, w, mk.m, tol=1e-6, precision="mixed", check=False,
+                              time_limit_s=limit_s)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    i = out.info
+    res = {"workload": "C2: n=1e6, m=1e4, 100 distinct uniform goods per buyer (nnz=1e8), LogNormal(0,1), "
+                       "w~U(0.5,1.5), MIXED, relative KKT 1e-6", "nnz": int(mk.nnz), "seconds": dt,
+           "status": int(out.status), "converged": int(out.status) == 0, "iters": int(i["iters"]),
+           "restarts": int(i["restarts"]), "kkt": i["kkt"], "r_primal": i["r_primal"], "r_dual": i["r_dual"],
+           "r_gap": i["r_gap"], "setup_s": i["setup_ms"] * 1e-3, "loop_s": i["solve_ms"] * 1e-3}
+    val64 = torch.from_numpy(mk.val.astype(np.float64)).to(dev)
+    res["fp64_iters_per_s"] = _gpu_iter_rate(solver, capi, torch, stream, rp, col, val64, w, mk.m,
+                                             capi.PDHCG_FP64, mk.nnz)["iters_per_s"]
+    res["mixed_iters_per_s"] = i["iters"] / max(i["solve_ms"] * 1e-3, 1e-9)
+    return res
+
+
 # the paper's Table tab:random-fisher rows (n, m, density; PDHCG and PDHG iterations and seconds on its GPU, to 1e-4)
 _RANDOM_FISHER_PAPER = (((1000, 400, 0.2), (2612, 1.7, 4303.8, 4.5)), ((10000, 4000, 0.02), (2758, 3.6, 7604, 7.1)),
                         ((100000, 4000, 0.02), (1200, 8.3, 10463, 29.9)))
@@ -747,9 +836,10 @@ def main():
     # default run: its top good sits in about every row, so ||K||_2 ~ 3e3 caps
     # the step size and the solve needs ~1e5+ iterations) ----
     ttt = None
+    parity = None
     if args.time_to_tol and rank == 0:
         ttt = _time_to_tol_c2(solver, capi, torch, stream, dev, S, args.ttt_limit_s)
-    solver.close()
+        parity = _oracle_parity_c3law(solver, torch, dev, S)
     solver.close()
 
     if rank != 0:
@@ -783,6 +873,8 @@ def main():
         line["time_to_tol"] = ttt
     if fp64:
         line["fp64_arm"] = fp64
+    if parity:
+        line["oracle_parity"] = parity
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

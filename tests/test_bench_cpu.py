@@ -44,3 +44,18 @@ def test_all_core_oracle_harness_matches_one_process():
     finally:
         one.close()
         two.close()
+
+
+def test_bench_names_resolve_and_stored_equilibrium_reads():
+    """Every module-level name bench.py's GPU path calls exists (the GPU path
+    cannot run here), and the stored oracle equilibrium it compares with reads."""
+    import ast
+    sys.path.insert(0, ROOT)
+    import bench
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    defined = {n.name for n in tree.body if isinstance(n, (ast.FunctionDef, ast.ClassDef))}
+    called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)
+              and n.func.id.startswith("_")}
+    assert called <= defined, called - defined
+    g = bench._stored_equilibrium("c3law_equilibrium.txt")
+    assert len(g["p"]) == 1000 and len(g["t"]) == 10000
