@@ -454,7 +454,8 @@ _JD_PAPER = ((3930, 7.0), (4839, 8.4), (5894, 12.4), (6865, 17.1), (10090, 41.3)
 def _study_jd(sol, S):
     """JD-shaped Fisher markets (Section 5.2): the n most active users of the
     synthetic click log for every size of Table tab:fisher, MIXED solves to
-    the paper's relative KKT 1e-4 (and to 1e-6 up to n = 2e5), 120 s cap each.
+    the paper's relative KKT 1e-4 (and to 1e-6 up to n = 2e5), 120 s cap each
+    (--study-cap-s overrides the cap).
     The paper's own iterations and times (other hardware) ride along as context."""
     import torch
     out = {"workload": "JD-shaped synthetic click log (Table tab:fisher prefix sizes exactly, products by "
@@ -468,7 +469,7 @@ def _study_jd(sol, S):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             o = sol.fisher_solve(*args, tol=tol, precision="mixed", max_iter=2_000_000, check=False,
-                                 time_limit_s=120.0)
+                                 time_limit_s=_STUDY_CAP_S or 120.0)
             torch.cuda.synchronize()
             row[f"tol_{tol:.0e}"] = {"status": int(o.status), "seconds": time.perf_counter() - t0,
                                      "iters": int(o.info["iters"]), "kkt": o.info["kkt"]}
@@ -691,6 +692,9 @@ def _study_pdhg(sol, S):
     return out
 
 
+_STUDY_CAP_S = None      # --study-cap-s: time cap of each solve of the JD study
+
+
 def run_study(which):
     import torch
     import __graft_entry__ as g
@@ -721,6 +725,7 @@ def main():
     ap.add_argument("--ttt-limit-s", type=float, default=300.0, help="time cap of the time-to-tolerance solve")
     ap.add_argument("--no-fp64-arm", dest="fp64_arm", action="store_false",
                     help="skip the plain FP64 GPU iterations/s on the same workload (on by default)")
+    ap.add_argument("--study-cap-s", type=float, default=None, help="time cap of each solve of --study jd")
     ap.add_argument("--study", choices=["c2", "c4", "c5", "jd", "ad", "sections", "pdhg"], default=None,
                     help="instead of the bench line, run one comparison study and print its JSON line")
     args = ap.parse_args()
@@ -734,6 +739,8 @@ def main():
         run_reference(args, cfg, rank)
         return
     if args.study:
+        global _STUDY_CAP_S
+        _STUDY_CAP_S = args.study_cap_s
         run_study(args.study)
         return
 

@@ -130,14 +130,11 @@ __device__ void rowm_core(const DevMarket& mk, float* __restrict__ Xout, const f
     const int* rj = R.j;
 #pragma unroll
     for (int k = 0; k < kSlots; k++) {
-        if (rj[k] >= 0) {
-            const float2 p = price_ff(pff, sp, mk.hot, rj[k]);
-            rph[k] = p.x;
-            rpl[k] = p.y;
-        } else {
-            rph[k] = 0.0f;
-            rpl[k] = 0.0f;
-        }
+        // selects, not a branch per slot: padding slots gather good 0 and zero it
+        const bool ok = rj[k] >= 0;
+        const float2 p = price_ff(pff, sp, mk.hot, ok ? rj[k] : 0);
+        rph[k] = ok ? p.x : 0.0f;
+        rpl[k] = ok ? p.y : 0.0f;
     }
     const float2 wv = valid ? mk.wff[row] : make_float2(1.0f, 0.0f);
     float2 y0 = valid ? yst[row] : make_float2(1.0f, 0.0f);
@@ -328,14 +325,10 @@ __device__ inline void rowm_long(const DevMarket& mk, const float* __restrict__ 
         }
 #pragma unroll
         for (int k = 0; k < kSlots; k++) {
-            if (rj[k] >= 0) {
-                const float2 p = price_ff(pff, sp, mk.hot, rj[k]);
-                rph[k] = p.x;
-                rpl[k] = p.y;
-            } else {
-                rph[k] = 0.0f;
-                rpl[k] = 0.0f;
-            }
+            const bool ok = rj[k] >= 0;
+            const float2 p = price_ff(pff, sp, mk.hot, ok ? rj[k] : 0);
+            rph[k] = ok ? p.x : 0.0f;
+            rpl[k] = ok ? p.y : 0.0f;
         }
     };
     auto td_at = [&](int k, float yh, float yl) -> float {
