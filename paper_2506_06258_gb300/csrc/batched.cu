@@ -1,5 +1,5 @@
 // Batched Fisher markets: B independent markets of uneven size solved by one
-// persistent kernel, captured in a CUDA graph.
+// launch of a persistent kernel.
 //
 // Each block takes the next market from a work queue (markets ordered by
 // decreasing nnz, an LPT schedule) and runs the whole of Alg. 2 on it:
@@ -843,32 +843,22 @@ pdhcg_status pdhcg_fisher_solve_batched(pdhcg_handle h, int32_t B, const int64_t
         launch_prep(mixed, a, mmax, s);
         CK(cudaGetLastError());
     }
-    // ---- the persistent launch, captured in a CUDA graph ----
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(a.queue, 0, 16, s);
-    launch_solve(mixed, a, grid, smem, s);
-    cudaError_t ce = cudaStreamEndCapture(s, &graph);
-    if (ce != cudaSuccess) return PDHCG_ERR_CUDA;
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    if (ce != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return PDHCG_ERR_CUDA;
-    }
+    // ---- the persistent launch (one kernel: nothing for a graph to batch) ----
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    ce = cudaGraphLaunch(exec, s);
+    cudaError_t ce = cudaMemsetAsync(a.queue, 0, 16, s);
+    if (ce == cudaSuccess) {
+        launch_solve(mixed, a, grid, smem, s);
+        ce = cudaGetLastError();
+    }
     cudaEventRecord(e1, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     float solve_ms = 0.0f;
     cudaEventElapsedTime(&solve_ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
     CK(ce);
     CK(cudaGetLastError());
     // ---- outputs ----
