@@ -28,6 +28,10 @@ constexpr double kFixInv = 1.0 / 1099511627776.0;
 constexpr float kFixScaleF = 1099511627776.0f;
 constexpr int kWarps = 8;                               // warps per block of the row kernels
 constexpr int kThreads = kWarps * 32;
+// the persistent row kernel: one block of 24 warps per SM (80 registers a
+// thread, one shared copy of the hot goods per SM)
+constexpr int kProxWarps = 24;
+constexpr int kProxThreads = kProxWarps * 32;
 constexpr int kMaxBuckets = 8;
 constexpr int kSlots = 4;                               // entries per lane held in registers
 constexpr int kPadEntries = 16;                         // slack after the nnz arrays

@@ -64,7 +64,7 @@ __device__ void bucket_mixed(const DevMarket& mk, const Bucket& bk, unsigned lon
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const void* Xin_fixed, void* Xout_fixed,
+__global__ void __launch_bounds__(kProxThreads, 1) prox_kernel(DevMarket mk, const void* Xin_fixed, void* Xout_fixed,
                                                          IterBufs bf, Ctl* ctl, int fixed) {
     extern __shared__ unsigned long long acc_s[];
     if (!ctl->active) return;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     // ---- block epilogue: ||dx||^2 partial, capped rows, flush hot column sums ----
     double v = MIXED ? (double)dxf : dxd;
     v = warp_sum_d(v);
-    __shared__ double red[kWarps];
+    __shared__ double red[kProxWarps];
     __shared__ int capred, evred;
     if (threadIdx.x == 0) capred = evred = 0;
     __syncthreads();
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 3) prox_kernel(DevMarket mk, const v
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kWarps; w++) t += red[w];
+        for (int w = 0; w < kProxWarps; w++) t += red[w];
         bf.part[blockIdx.x] = t;
         if (capred) atomicAdd((unsigned long long*)&ctl->capped, (unsigned long long)capred);
         if (evred) atomicAdd((unsigned long long*)&ctl->evals, (unsigned long long)evred);
@@ -441,8 +441,8 @@ int prox_blocks(bool mixed, int hot) {
     set_smem_attr();
     int per = 0;
     size_t smem = prox_smem_bytes(mixed, hot);
-    if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prox_kernel<true>, kThreads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prox_kernel<false>, kThreads, smem);
+    if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prox_kernel<true>, kProxThreads, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prox_kernel<false>, kProxThreads, smem);
     if (per < 1) per = 1;
     const char* env = getenv("PDHCG_PROX_BLOCKS_PER_SM");
     if (env && atoi(env) > 0 && atoi(env) < per) per = atoi(env);
@@ -461,8 +461,8 @@ void launch_price(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, 
 }
 void launch_prox(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s) {
     set_smem_attr();
-    if (mixed) prox_kernel<true><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, nullptr, nullptr, b, ctl, 0);
-    else prox_kernel<false><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, nullptr, nullptr, b, ctl, 0);
+    if (mixed) prox_kernel<true><<<mk.nprox, kProxThreads, prox_smem(mk), s>>>(mk, nullptr, nullptr, b, ctl, 0);
+    else prox_kernel<false><<<mk.nprox, kProxThreads, prox_smem(mk), s>>>(mk, nullptr, nullptr, b, ctl, 0);
 }
 void launch_dual(bool mixed, const DevMarket& mk, const IterBufs& b, Ctl* ctl, cudaStream_t s) {
     int nb = vec_blocks(mk.m);
@@ -553,10 +553,10 @@ void launch_prox_fixed(bool mixed, const DevMarket& mk, const void* x_in, void* 
     ctl_fixed_kernel<<<1, 1, 0, s>>>(ctl, tau, 64);
     if (mixed) {
         yfill_kernel<<<vec_blocks(mk.n), 256, 0, s>>>(mk.n, b.yst);
-        prox_kernel<true><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
+        prox_kernel<true><<<mk.nprox, kProxThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
         y_to_s_kernel<<<vec_blocks(mk.n), 256, 0, s>>>(mk.n, mk.w, t_out);
     } else {
-        prox_kernel<false><<<mk.nprox, kThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
+        prox_kernel<false><<<mk.nprox, kProxThreads, prox_smem(mk), s>>>(mk, x_in, x_out, b, ctl, 1);
     }
     cols_out_kernel<<<vec_blocks(mk.m), 256, 0, s>>>(mk.m, mixed, acc, c_out);
 }
