@@ -10,7 +10,8 @@
 // (maxima over the support of U).  Two kernels: a row pass (one warp per row:
 // t_i, y_i, the per-entry gap terms, the column maxima M_j and the column sums)
 // and a goods pass whose last block (last-block-done ticket, no spin) combines
-// every partial into KktOut.  Products and maxima are in FP64.
+// every partial into KktOut.  Products and maxima are in FP64 for FP64 markets;
+// the MIXED row pass forms t and y in float-float and its maxima in FP32.
 #include "common.cuh"
 
 namespace pdhcg {
@@ -113,22 +114,28 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_mixed_kernel(DevMarket mk, 
     const int lane = threadIdx.x & 31;
     const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * kWarps;
-    float mx = 0.0f, mg = 0.0f, mxg = 0.0f, mnd = 0.0f;
-    double my = 0.0;
+    float mx = 0.0f, mg = 0.0f, mxg = 0.0f, mnd = 0.0f, my = 0.0f;
     for (long long i = gw; i < mk.n; i += nw) {
         const long long b = mk.rp[i], e = mk.rp[i + 1];
-        ff t = ff_make(0.0f, 0.0f);
+        // t = u_i^T x_i in float-float: TwoProduct terms, their high parts
+        // summed by TwoSum, every low part added in FP32
+        float th = 0.0f, tl = 0.0f;
         float um = 0.0f;
         for (long long q = b + lane; q < e; q += 32) {
             const float u = U[q];
-            t = ff_add(t, two_prod(u, Xv[q]));
+            const ff pr = two_prod(u, Xv[q]);
+            const ff sm = two_sum(th, pr.hi);
+            th = sm.hi;
+            tl += sm.lo + pr.lo;
             um = fmaxf(um, u);
         }
-        t = group_sum<32>(t);
+        const ff t = group_sum<32>(ff_make(th, tl));
         for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
-        const ff y = ff_div(ff_from_double(mk.w[i]), t);
+        // budgets as float-float (no FP64 per row: FP64 is a slow pipe here)
+        const ff wi = mk.wff ? ff_make(mk.wff[i].x, mk.wff[i].y) : ff_from_double(mk.w[i]);
+        const ff y = ff_div(wi, t);
         if (lane == 0 && kb.t_out) kb.t_out[i] = ff_to_double(t);
-        my = fmax(my, ff_to_double(y) * (double)um);   // y of the max-scaled row
+        my = fmaxf(my, (y.hi + y.lo) * um);   // y of the max-scaled row
         for (long long q = b + lane; q < e; q += 32) {
             const int j = mk.cj[q];
             const float u = U[q], x = Xv[q];
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_mixed_kernel(DevMarket mk, 
         mxg = fmaxf(mxg, __shfl_xor_sync(0xffffffffu, mxg, o));
         mnd = fmaxf(mnd, __shfl_xor_sync(0xffffffffu, mnd, o));
     }
-    my = warp_max_d(my);
+    for (int o = 16; o > 0; o >>= 1) my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
     __shared__ KktPart red[kWarps];
     __shared__ float red2[kWarps];
     if (lane == 0) { red[threadIdx.x >> 5] = KktPart{mx, mg, mxg, my}; red2[threadIdx.x >> 5] = mnd; }
