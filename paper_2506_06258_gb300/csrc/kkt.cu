@@ -115,19 +115,62 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_mixed_kernel(DevMarket mk, 
     const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * kWarps;
     float mx = 0.0f, mg = 0.0f, mxg = 0.0f, mnd = 0.0f, my = 0.0f;
+    // one entry of the second pass: gap terms, column minimum of p_j - u_ij y_i, column sum
+    auto entry = [&](int j, float u, float x, float2 p, ff y) {
+        const float d = fmaf(-u, y.lo, fmaf(-u, y.hi, p.x) + p.y);   // p_j - u_ij y_i
+        const float g = fmaxf(d, 0.0f);
+        mx = fmaxf(mx, x);
+        mg = fmaxf(mg, g);
+        mxg = fmaxf(mxg, x * g);
+        mnd = fmaxf(mnd, -d);
+        const int key = fkey(d);
+        if (j < mk.hot) {
+            if (key < dmin_s[j]) shared_min_s32(&dmin_s[j], key);
+            if (x > 0.0f) shared_add_u64(&acc_s[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));
+        } else {
+            if (key < ((volatile int*)dmin_g)[j]) atomicMin(&dmin_g[j], key);
+            if (x > 0.0f) atomicAdd(&kb.acc[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));
+        }
+    };
     for (long long i = gw; i < mk.n; i += nw) {
         const long long b = mk.rp[i], e = mk.rp[i + 1];
+        // rows of at most 32 * kSlots entries are read once into registers
+        // (lane l holds entries l, l + 32, ...), longer ones are streamed twice;
+        // either way a lane visits its entries in increasing order
+        const bool reg = e - b <= 32 * kSlots;
+        float ru[kSlots], rx[kSlots];
+        int rj[kSlots];
         // t = u_i^T x_i in float-float: TwoProduct terms, their high parts
         // summed by TwoSum, every low part added in FP32
         float th = 0.0f, tl = 0.0f;
         float um = 0.0f;
-        for (long long q = b + lane; q < e; q += 32) {
-            const float u = U[q];
-            const ff pr = two_prod(u, Xv[q]);
-            const ff sm = two_sum(th, pr.hi);
-            th = sm.hi;
-            tl += sm.lo + pr.lo;
-            um = fmaxf(um, u);
+        if (reg) {
+#pragma unroll
+            for (int k = 0; k < kSlots; k++) {
+                const long long q = b + lane + 32 * k;
+                const bool in = q < e;
+                rj[k] = in ? mk.cj[q] : -1;
+                ru[k] = in ? U[q] : 0.0f;
+                rx[k] = in ? Xv[q] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < kSlots; k++) {
+                if (rj[k] < 0) continue;
+                const ff pr = two_prod(ru[k], rx[k]);
+                const ff sm = two_sum(th, pr.hi);
+                th = sm.hi;
+                tl += sm.lo + pr.lo;
+                um = fmaxf(um, ru[k]);
+            }
+        } else {
+            for (long long q = b + lane; q < e; q += 32) {
+                const float u = U[q];
+                const ff pr = two_prod(u, Xv[q]);
+                const ff sm = two_sum(th, pr.hi);
+                th = sm.hi;
+                tl += sm.lo + pr.lo;
+                um = fmaxf(um, u);
+            }
         }
         const ff t = group_sum<32>(ff_make(th, tl));
         for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
@@ -136,23 +179,17 @@ __global__ void __launch_bounds__(kThreads) kkt_rows_mixed_kernel(DevMarket mk, 
         const ff y = ff_div(wi, t);
         if (lane == 0 && kb.t_out) kb.t_out[i] = ff_to_double(t);
         my = fmaxf(my, (y.hi + y.lo) * um);   // y of the max-scaled row
-        for (long long q = b + lane; q < e; q += 32) {
-            const int j = mk.cj[q];
-            const float u = U[q], x = Xv[q];
-            const float2 p = kb.pff[j];
-            const float d = fmaf(-u, y.lo, fmaf(-u, y.hi, p.x) + p.y);   // p_j - u_ij y_i
-            const float g = fmaxf(d, 0.0f);
-            mx = fmaxf(mx, x);
-            mg = fmaxf(mg, g);
-            mxg = fmaxf(mxg, x * g);
-            mnd = fmaxf(mnd, -d);
-            const int key = fkey(d);
-            if (j < mk.hot) {
-                if (key < dmin_s[j]) shared_min_s32(&dmin_s[j], key);
-                if (x > 0.0f) shared_add_u64(&acc_s[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));
-            } else {
-                if (key < ((volatile int*)dmin_g)[j]) atomicMin(&dmin_g[j], key);
-                if (x > 0.0f) atomicAdd(&kb.acc[j], (unsigned long long)__float2ll_rn(x * kFixScaleF));
+        if (reg) {
+            float2 pp[kSlots];
+#pragma unroll
+            for (int k = 0; k < kSlots; k++) pp[k] = kb.pff[rj[k] >= 0 ? rj[k] : 0];   // gathers issued together
+#pragma unroll
+            for (int k = 0; k < kSlots; k++)
+                if (rj[k] >= 0) entry(rj[k], ru[k], rx[k], pp[k], y);
+        } else {
+            for (long long q = b + lane; q < e; q += 32) {
+                const int j = mk.cj[q];
+                entry(j, U[q], Xv[q], kb.pff[j], y);
             }
         }
     }
